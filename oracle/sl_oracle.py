@@ -1,0 +1,819 @@
+"""FP64 CPU oracle for the explicit semi-Lagrangian spectral (DSEM-SL) transport step.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import or run this module.  The CUDA library never calls it, and it
+shares no code, tables or helpers with the CUDA library: nodes, weights, basis values and
+all operators are recomputed here from their definitions, with different algorithms
+(eigenvalues of the Jacobi matrix instead of Newton, the Lagrange product formula instead of
+the barycentric form, a pivoted-QR least-squares fit instead of precomputed operators).
+
+Everything is plain numpy in float64, one element at a time, with every intermediate of
+the step materialised.  Sections of the paper (arXiv:1910.06476) that each function follows
+are cited in its docstring.
+
+Readings taken where the paper is silent, garbled or at odds with itself (each is listed
+in the design notes):
+  R1  Gauss node formula (Sec. 3, eq. gaussquad): n = N+1 Chebyshev-Gauss points
+      xi_i = (1 - cos((i + 1/2) pi / n)) / 2, i = 0..n-1.  Gauss-Legendre is also offered.
+  R2  Quadrature weights for Chebyshev-Gauss nodes (eq. quad): the interpolatory weights
+      w_i = integral_0^1 l_i (Fejer's first rule); for Gauss-Legendre they are the GL weights.
+  R3  Particles are integrated in physical coordinates (eq. 4.4 writes u(xi)).
+  R4  Each boundary-constraint row pairs with the upwinded value of the same face (matrix_a).
+  R5  Mass target: M^{n+1} = M^n - dt * (net outflow), i.e. inflow adds mass (eq. remap_mass
+      vs matrix_a disagree in sign).  Over the step the face flux is integrated with the RK
+      quadrature (b_s, c_s); the face value at stage time tau is the upwind element's phi^n
+      polynomial at the backward characteristic foot of (x_face, tau) (one RK step of the
+      same scheme run backward, possibly slightly outside that element).  RK1 gives the
+      paper's first-order formula.  Energy uses phi^2 the same way (eq. remap_energy).
+  R6  Hard constraints (default): lexicographic least squares -- minimise |C phi - d| and,
+      among minimisers, |phi - phihat| (the pseudo-inverse solution).  Soft (paper-literal
+      stacked least squares of matrix_a) is offered as FIT_SOFT.
+  R7  Energy: the paper's Picard linearisation (row h w o phi^(k-1)) has derivative -1 at its
+      fixed point and cycles with period two (scalar case: phi_k = c / phi_{k-1}).  In the
+      hard fit we keep its fixed point and reach it by taking the Picard correction
+      direction from the previous iterate and solving the energy equation exactly along it
+      (a scalar quadratic, smallest root).  The soft fit iterates the paper's system as is.
+  R8  Upwinding by the sign of u.n at the face point (at t^{n+1} for boundary values, at the
+      stage time for fluxes); |u.n| <= TIE is a tie: interior faces average both traces,
+      non-periodic domain faces keep their own trace.
+  R9  Time step (eq. 1d_delt_condition, 2d_delt_condition): rule 'paper' uses the gap from
+      the element edge to the first node with factor 1; rule 'half_min_spacing' uses half
+      the minimum spacing between adjacent nodes.
+  R10 p-nonconforming faces: the upwind neighbour's polynomial is evaluated at this element's
+      face points; face fluxes use the Gauss rule of the side with more nodes.
+
+Parity pins (see tests/test_oracle_*.py): nodes/weights against numpy's leggauss and
+monomial exactness; basis cardinality and polynomial reproduction; exact translation of
+polynomial data; exact 2D Kronecker collocation; constraint satisfaction to round-off;
+global mass/energy telescoping; exponential convergence in N; the paper's time step
+1.97e-2 (Sec. 5.2).  Parity unpinned: the MF/MEF error values of the paper's tables.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg
+
+GAUSS_LEGENDRE, CHEB_GAUSS = 0, 1
+VEL_CONST, VEL_ROTATION, VEL_SWIRL, VEL_SINX = 0, 1, 2, 3
+BC_PERIODIC, BC_INFLOW = 0, 1
+C_BOUNDARY, C_MASS, C_ENERGY = 1, 2, 4
+FIT_HARD, FIT_SOFT = 0, 1
+BV_INTERP, BV_BACKTRACK = 0, 1
+
+TIE = 1e-13                 # |u.n| at or below this is a tie (R8)
+RANK_RTOL = 1e-12           # rank decision of the pivoted QR (R6)
+PICARD_RTOL = 1e-13         # default energy-iteration tolerance, relative to max|phihat| (R7)
+PICARD_CAP = 60
+
+# ============================================================================ L0 tables
+
+
+def gauss_legendre_01(n):
+    """Gauss-Legendre nodes and weights on [0, 1] via the Golub-Welsch eigenvalue method.
+
+    The solution nodes of the method are Gauss points (Sec. 3); the Legendre family is the
+    one the large synthetic workloads use.  Jacobi matrix of the Legendre recurrence:
+    off-diagonal k / sqrt(4k^2 - 1); nodes are its eigenvalues, weights 2 v_0^2."""
+    if n == 1:
+        return np.array([0.5]), np.array([1.0])
+    k = np.arange(1, n, dtype=np.float64)
+    off = k / np.sqrt(4.0 * k * k - 1.0)
+    J = np.diag(off, 1) + np.diag(off, -1)
+    vals, vecs = np.linalg.eigh(J)
+    order = np.argsort(vals)
+    x = vals[order]
+    w = 2.0 * vecs[0, order] ** 2
+    x = 0.5 * (x - x[::-1])          # symmetrise rounding
+    w = 0.5 * (w + w[::-1])
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def chebyshev_gauss_01(n):
+    """Chebyshev-Gauss solution nodes on [0, 1], Sec. 3 eq. gaussquad under reading R1."""
+    i = np.arange(n, dtype=np.float64)
+    return 0.5 * (1.0 - np.cos((i + 0.5) * np.pi / n))
+
+
+def lagrange(nodes, x):
+    """Lagrange basis on ``nodes`` evaluated at points ``x`` (Sec. 3 eq. 3.5, Sec. 4.1 eq. 4.3).
+
+    Plain product formula l_j(x) = prod_{m != j} (x - x_m) / (x_j - x_m).
+    Returns an array of shape (len(x), len(nodes))."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    n = nodes.size
+    L = np.ones((x.size, n))
+    for j in range(n):
+        for m in range(n):
+            if m != j:
+                L[:, j] *= (x - nodes[m]) / (nodes[j] - nodes[m])
+    return L
+
+
+def interpolatory_weights(nodes):
+    """w_j = integral_0^1 l_j(xi) d xi (reading R2), integrated exactly by a Gauss rule."""
+    gx, gw = gauss_legendre_01(len(nodes) + 1)
+    return lagrange(nodes, gx).T @ gw
+
+
+def nodes_weights(n, basis):
+    """Solution nodes and quadrature weights (eq. gaussquad, eq. quad) on [0, 1]."""
+    if basis == GAUSS_LEGENDRE:
+        return gauss_legendre_01(n)
+    if basis == CHEB_GAUSS:
+        xi = chebyshev_gauss_01(n)
+        return xi, interpolatory_weights(xi)
+    raise ValueError("unknown basis")
+
+
+# ============================================================================ velocity
+
+
+@dataclass
+class Vel:
+    kind: int
+    p: tuple
+
+
+def velocity(vel, x, y, t):
+    """Prescribed velocity (u, v) and its divergence at physical points (Sec. 4.2).
+
+    CONST (a, b) as in Sec. 5.1 / 5.3; ROTATION (omega, cx, cy) solid-body rotation;
+    SWIRL (T,) the periodic swirling deformation flow; SINX u = -sin x of Sec. 5.2."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64) if y is not None else np.zeros_like(x)
+    z = np.zeros_like(x)
+    p = vel.p
+    if vel.kind == VEL_CONST:
+        return z + p[0], z + p[1], z
+    if vel.kind == VEL_ROTATION:
+        om, cx, cy = p[0], p[1], p[2]
+        return -om * (y - cy), om * (x - cx), z      # divergence-free
+    if vel.kind == VEL_SWIRL:
+        c = math.cos(math.pi * t / p[0])
+        u = np.sin(np.pi * x) ** 2 * np.sin(2.0 * np.pi * y) * c
+        v = -(np.sin(np.pi * y) ** 2) * np.sin(2.0 * np.pi * x) * c
+        return u, v, z                                 # divergence-free
+    if vel.kind == VEL_SINX:
+        return -np.sin(x), z, -np.cos(x)
+    raise ValueError("unknown velocity kind")
+
+
+def max_speed(vel, box):
+    """|u|max and |v|max over the domain (used by the time-step rule)."""
+    p = vel.p
+    if vel.kind == VEL_CONST:
+        return abs(p[0]), abs(p[1])
+    if vel.kind == VEL_ROTATION:
+        x0, x1, y0, y1 = box
+        om = abs(p[0])
+        return (om * max(abs(y0 - p[2]), abs(y1 - p[2])),
+                om * max(abs(x0 - p[1]), abs(x1 - p[1])))
+    if vel.kind == VEL_SWIRL:
+        return 1.0, 1.0
+    if vel.kind == VEL_SINX:
+        return 1.0, 0.0
+    raise ValueError
+
+
+# ============================================================================ RK
+
+
+def rk_tableau(order):
+    """Explicit RK schemes for orders 1-4 (forward Euler, Heun, Kutta's third order, classical)."""
+    if order == 1:
+        return np.zeros((1, 1)), np.array([1.0]), np.array([0.0])
+    if order == 2:
+        return np.array([[0, 0], [1.0, 0]]), np.array([0.5, 0.5]), np.array([0.0, 1.0])
+    if order == 3:
+        A = np.array([[0, 0, 0], [0.5, 0, 0], [-1.0, 2.0, 0]])
+        return A, np.array([1 / 6, 2 / 3, 1 / 6]), np.array([0.0, 0.5, 1.0])
+    if order == 4:
+        A = np.array([[0, 0, 0, 0], [0.5, 0, 0, 0], [0, 0.5, 0, 0], [0, 0, 1.0, 0]])
+        return A, np.array([1 / 6, 1 / 3, 1 / 3, 1 / 6]), np.array([0.0, 0.5, 0.5, 1.0])
+    raise ValueError("rk order must be 1..4")
+
+
+def rk_particles(vel, x, y, phi, t, h, order):
+    """One explicit RK step of dx/dt = u, dy/dt = v, dphi/dt = -phi div u (eq. 2.5, 2.4,
+    4.4a, 4.8), of size h (negative h runs the characteristic backward)."""
+    A, b, c = rk_tableau(order)
+    s = len(b)
+    kx, ky, kp = [], [], []
+    for i in range(s):
+        xi = x + h * sum(A[i, j] * kx[j] for j in range(i))
+        yi = y + h * sum(A[i, j] * ky[j] for j in range(i))
+        pi = phi + h * sum(A[i, j] * kp[j] for j in range(i))
+        u, v, dv = velocity(vel, xi, yi, t + c[i] * h)
+        kx.append(u)
+        ky.append(v)
+        kp.append(-pi * dv)
+    xn = x + h * sum(b[i] * kx[i] for i in range(s))
+    yn = y + h * sum(b[i] * ky[i] for i in range(s))
+    pn = phi + h * sum(b[i] * kp[i] for i in range(s))
+    return xn, yn, pn
+
+
+# ============================================================================ mesh
+
+
+@dataclass
+class Setup:
+    """Mesh and discretisation: uniform rectangles (Sec. 3 with an affine map)."""
+    dim: int
+    kx: int
+    ky: int
+    box: tuple
+    n: int
+    basis: int = GAUSS_LEGENDRE
+    bc: tuple = (BC_PERIODIC,) * 4
+    ghost: object = 0.0          # constant, or callable ghost(x, y, t) for inflow faces
+    orders: object = None        # optional (ky, kx) per-element node counts
+
+    @property
+    def hx(self):
+        return (self.box[1] - self.box[0]) / self.kx
+
+    @property
+    def hy(self):
+        return (self.box[3] - self.box[2]) / self.ky if self.dim == 2 else 1.0
+
+    def n_of(self, ex, ey=0):
+        return int(self.orders[ey, ex]) if self.orders is not None else self.n
+
+
+def setup_from_problem(prob):
+    return Setup(prob.dim, prob.kx, prob.ky, prob.box, prob.n, prob.basis, prob.bc,
+                 prob.ghost, prob.orders)
+
+
+@dataclass
+class StepOpts:
+    vel: Vel
+    t: float
+    dt: float
+    constraints: int = C_BOUNDARY
+    rk_order: int = 4
+    fit: int = FIT_HARD
+    bvalue: int = BV_INTERP
+    picard_tol: float = None     # absolute; None -> PICARD_RTOL * max|phihat|
+    picard_cap: int = PICARD_CAP
+
+
+def _ghost(setup, x, y, t):
+    g = setup.ghost
+    if callable(g):
+        return g(x, y, t)
+    return np.zeros_like(np.asarray(x, dtype=np.float64)) + g
+
+
+def max_dt(setup, vel, rule="half_min_spacing", cfl=None):
+    """Time-step limit, eq. 1d_delt_condition / 2d_delt_condition under reading R9."""
+    xi, _ = nodes_weights(setup.n if setup.orders is None else int(setup.orders.max()), setup.basis)
+    if setup.orders is not None:
+        gaps = []
+        for n in np.unique(setup.orders):
+            xn, _ = nodes_weights(int(n), setup.basis)
+            gaps.append(np.min(np.diff(xn)) if rule == "half_min_spacing" else xn[0])
+        gap = min(gaps)
+    else:
+        gap = np.min(np.diff(xi)) if rule == "half_min_spacing" else xi[0]
+    factor = (0.5 if rule == "half_min_spacing" else 1.0) if cfl is None else cfl
+    umax, vmax = max_speed(vel, setup.box)
+    lims = []
+    if umax > 0:
+        lims.append(setup.hx * gap / umax)
+    if setup.dim == 2 and vmax > 0:
+        lims.append(setup.hy * gap / vmax)
+    return factor * min(lims)
+
+
+# ============================================================================ fit
+
+
+def fit_hard(phihat, C, d):
+    """Lexicographic least squares (R6): among minimisers of |C phi - d|, the one nearest phihat.
+
+    Complete orthogonal decomposition via Householder QR with column pivoting of C^T."""
+    if C.shape[0] == 0:
+        return phihat.copy()
+    r = d - C @ phihat
+    Q, R, P = scipy.linalg.qr(C.T, mode="economic", pivoting=True)
+    diag = np.abs(np.diag(R))
+    if diag.size == 0 or diag[0] == 0.0:
+        return phihat.copy()
+    p = int(np.sum(diag > RANK_RTOL * diag[0]))
+    z, *_ = np.linalg.lstsq(R[:p, :].T, r[P], rcond=None)
+    return phihat + Q[:, :p] @ z
+
+
+def fit_soft(phihat, C, d):
+    """The paper's over-determined system (eq. matrix_a): identity rows stacked on the
+    constraint rows, solved by ordinary least squares."""
+    n = phihat.size
+    A = np.vstack([np.eye(n), C])
+    rhs = np.concatenate([phihat, d])
+    sol, *_ = np.linalg.lstsq(A, rhs, rcond=None)
+    return sol
+
+
+def energy_step_scalar(alpha, beta, gamma):
+    """Smallest root s of beta s^2 + 2 alpha s + gamma = 0 (energy of phi_L + s q equals the
+    target); without a real root, the s of least energy.  Returns (s, feasible)."""
+    if beta <= 0.0:
+        return 0.0, gamma <= 0.0
+    disc = alpha * alpha - beta * gamma
+    if disc < 0.0:
+        return -alpha / beta, False
+    root = math.sqrt(disc)
+    den = alpha + (root if alpha >= 0.0 else -root)
+    if den == 0.0:
+        return 0.0, True
+    return -gamma / den, True
+
+
+def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode, tol, cap):
+    """Least-squares remap with linear constraints and optional energy (Sec. 4.3, matrix_a).
+
+    ``energy_row_weights`` (h^d w o w, flattened) switches the energy constraint on; its row
+    is (weights o phi^(k-1)), iterated over k until max|phi^(k) - phi^(k-1)| < tol.
+    Hard fit (reading R7): the correction direction of that row, q = P a^(k) with P the
+    projector onto the null space of the linear rows, is taken from the previous iterate and
+    the energy equation is solved exactly along it.  Soft fit: the paper's stacked system
+    with the linearised energy row, iterated literally.
+    Returns (phi, iterations, converged)."""
+    if fit_mode == FIT_HARD:
+        phiL = fit_hard(phihat, C_lin, d_lin)
+        if energy_row_weights is None:
+            return phiL, 0, True
+        W = energy_row_weights
+        gamma = float(np.dot(W, phiL * phiL)) - E_target
+        phi = phiL
+        feasible = True
+        for it in range(1, cap + 1):
+            a = W * phi
+            q = fit_hard(a, C_lin, np.zeros_like(d_lin))        # P a
+            alpha = float(np.dot(W, phiL * q))
+            beta = float(np.dot(W, q * q))
+            s, feasible = energy_step_scalar(alpha, beta, gamma)
+            new = phiL + s * q
+            delta = float(np.max(np.abs(new - phi)))
+            phi = new
+            if delta < tol:
+                return phi, it, feasible
+        return phi, cap, False
+    phi = fit_soft(phihat, C_lin, d_lin)
+    if energy_row_weights is None:
+        return phi, 0, True
+    for it in range(1, cap + 1):
+        a = energy_row_weights * phi
+        new = fit_soft(phihat, np.vstack([C_lin, a[None, :]]), np.concatenate([d_lin, [E_target]]))
+        delta = float(np.max(np.abs(new - phi)))
+        phi = new
+        if delta < tol:
+            return phi, it, True
+    return phi, cap, False
+
+
+# ============================================================================ 1D step
+
+
+def _elem_geom_1d(setup, k):
+    n = setup.n
+    xi, w = nodes_weights(n, setup.basis)
+    xk = setup.box[0] + k * setup.hx
+    return xi, w, xk
+
+
+def _advected_1d(setup, k, phi_k, o):
+    """Steps (a)-(b): seed particles at the Gauss nodes and integrate them (Sec. 4.1-4.2)."""
+    xi, w, xk = _elem_geom_1d(setup, k)
+    X = xk + setup.hx * xi
+    Xs, _, Ps = rk_particles(o.vel, X, np.zeros_like(X), phi_k.astype(np.float64), o.t, o.dt,
+                             o.rk_order)
+    return (Xs - xk) / setup.hx, Ps
+
+
+def remap_1d(setup, k, phi_k, o):
+    """Remap by interpolation, eq. 4.9 / remap_advect: phihat_j = sum_i phi*_i h*_i(xi_j)."""
+    xi, _, _ = _elem_geom_1d(setup, k)
+    xs, ps = _advected_1d(setup, k, phi_k, o)
+    return lagrange(xs, xi) @ ps
+
+
+def traces_1d(setup, k, phi_k, o):
+    """Interface values of element k at t^{n+1} at its (left, right) faces.
+
+    BV_INTERP: the advected polynomial at the face, eq. remap_bnd.
+    BV_BACKTRACK: phi^n of this element at the backward foot of the face point, eq. 4.11."""
+    xi, _, xk = _elem_geom_1d(setup, k)
+    if o.bvalue == BV_INTERP:
+        xs, ps = _advected_1d(setup, k, phi_k, o)
+        return lagrange(xs, [0.0, 1.0]) @ ps
+    xf = np.array([xk, xk + setup.hx])
+    tn1 = o.t + o.dt
+    fx, _, fac = rk_particles(o.vel, xf, np.zeros(2), np.ones(2), tn1, -o.dt, o.rk_order)
+    return (lagrange(xi, (fx - xk) / setup.hx) @ phi_k) / fac
+
+
+def _nb_1d(setup, k, side):
+    """Neighbour index across the left (side=0) or right (side=1) face; None at a
+    non-periodic domain boundary."""
+    K = setup.kx
+    j = k - 1 if side == 0 else k + 1
+    if 0 <= j < K:
+        return j
+    if setup.bc[side] == BC_PERIODIC:
+        return j % K
+    return None
+
+
+def _face_value_1d(setup, phi, k, side, o):
+    """Upwinded unique interface value at face ``side`` of element k (eq. 4.12a, R8)."""
+    xk = setup.box[0] + k * setup.hx
+    xf = xk + (setup.hx if side == 1 else 0.0)
+    nout = 1.0 if side == 1 else -1.0
+    u, _, _ = velocity(o.vel, np.array([xf]), None, o.t + o.dt)
+    un = float(u[0]) * nout
+    own = traces_1d(setup, k, phi[k], o)[side]
+    j = _nb_1d(setup, k, side)
+    if j is None:
+        other = float(_ghost(setup, np.array([xf]), np.array([0.0]), o.t + o.dt)[0])
+        if abs(un) <= TIE:
+            return own
+    else:
+        other = traces_1d(setup, j, phi[j], o)[1 - side]
+    if un > TIE:
+        return own
+    if un < -TIE:
+        return other
+    return 0.5 * (own + other)
+
+
+def _poly_at_1d(setup, phi, e, xq):
+    xi, _, xe = _elem_geom_1d(setup, e)
+    return lagrange(xi, (np.atleast_1d(xq) - xe) / setup.hx) @ phi[e]
+
+
+def _face_flux_1d(setup, phi, k, side, o, power):
+    """Outward flux of phi^power through face ``side`` of element k over the step (R5)."""
+    xk = setup.box[0] + k * setup.hx
+    xf = xk + (setup.hx if side == 1 else 0.0)
+    nout = 1.0 if side == 1 else -1.0
+    _, b, c = rk_tableau(o.rk_order)
+    total = 0.0
+    for s in range(len(b)):
+        tau = o.t + c[s] * o.dt
+        u, _, _ = velocity(o.vel, np.array([xf]), None, tau)
+        un = float(u[0]) * nout
+        if abs(un) <= TIE:
+            continue
+        up = k if un > 0 else _nb_1d(setup, k, side)
+        if up is None:
+            val = float(_ghost(setup, np.array([xf]), np.array([0.0]), tau)[0])
+        else:
+            if c[s] == 0.0:
+                foot, fac = np.array([xf]), np.array([1.0])
+            else:
+                foot, _, fac = rk_particles(o.vel, np.array([xf]), np.zeros(1), np.ones(1), tau,
+                                            -c[s] * o.dt, o.rk_order)
+            shift = 0.0
+            if up != k:     # express the foot in the neighbour's frame across a periodic wrap
+                jj = k - 1 if side == 0 else k + 1
+                shift = (up - jj) * setup.hx
+            val = float(_poly_at_1d(setup, phi, up, foot + shift)[0] / fac[0])
+        total += b[s] * un * val ** power
+    return total
+
+
+def element_step_1d(setup, phi, k, o):
+    """One DSEM-SL step for element k of a 1D mesh (Sec. 4, steps a-d).
+
+    ``phi`` is the whole pre-step state (K, n); only element k and its face neighbours are
+    read.  Returns (phi_new_k, info dict)."""
+    xi, w, xk = _elem_geom_1d(setup, k)
+    h = setup.hx
+    phihat = remap_1d(setup, k, phi[k], o)
+    rows, rhs = [], []
+    if o.constraints & C_BOUNDARY:
+        Lb = lagrange(xi, [0.0, 1.0])
+        for side in (0, 1):
+            rows.append(Lb[side])
+            rhs.append(_face_value_1d(setup, phi, k, side, o))
+    if o.constraints & C_MASS:
+        Mn = h * np.dot(w, phi[k])
+        F = _face_flux_1d(setup, phi, k, 0, o, 1) + _face_flux_1d(setup, phi, k, 1, o, 1)
+        rows.append(h * w)
+        rhs.append(Mn - o.dt * F)
+    C = np.array(rows).reshape(len(rows), xi.size)
+    d = np.array(rhs, dtype=np.float64)
+    ew, Et = None, 0.0
+    if o.constraints & C_ENERGY:
+        En = h * np.dot(w, phi[k] ** 2)
+        F = _face_flux_1d(setup, phi, k, 0, o, 2) + _face_flux_1d(setup, phi, k, 1, o, 2)
+        ew, Et = h * w, En - o.dt * F
+    tol = o.picard_tol if o.picard_tol is not None else PICARD_RTOL * max(np.max(np.abs(phihat)), 1e-300)
+    new, iters, conv = constrained_fit(phihat, C, d, ew, Et, o.fit, tol, o.picard_cap)
+    return new, {"phihat": phihat, "C": C, "d": d, "iters": iters, "converged": conv,
+                 "E_target": Et}
+
+
+def step_1d(setup, phi, o, elements=None):
+    """Advance a 1D state (K, n) by one step; ``elements`` restricts to a sample (the other
+    rows are returned unchanged).  Returns (phi_new, infos)."""
+    phi = np.asarray(phi, dtype=np.float64)
+    out = phi.copy()
+    infos = {}
+    ks = range(setup.kx) if elements is None else elements
+    for k in ks:
+        out[k], infos[int(k)] = element_step_1d(setup, phi, int(k), o)
+    return out, infos
+
+
+# ============================================================================ 2D step
+# element state layout: phi_e[j, i], j along y (eta), i along x (xi)
+
+
+def _elem_nodes_2d(setup, ex, ey):
+    n = setup.n_of(ex, ey)
+    xi, w = nodes_weights(n, setup.basis)
+    x0 = setup.box[0] + ex * setup.hx
+    y0 = setup.box[2] + ey * setup.hy
+    return n, xi, w, x0, y0
+
+
+def _get(phi, ex, ey):
+    return phi[ey][ex]
+
+
+def _advected_2d(setup, phi, ex, ey, o):
+    n, xi, w, x0, y0 = _elem_nodes_2d(setup, ex, ey)
+    XX = x0 + setup.hx * np.broadcast_to(xi[None, :], (n, n))
+    YY = y0 + setup.hy * np.broadcast_to(xi[:, None], (n, n))
+    Xs, Ys, Ps = rk_particles(o.vel, XX.ravel(), YY.ravel(), _get(phi, ex, ey).ravel().astype(np.float64),
+                              o.t, o.dt, o.rk_order)
+    return (Xs - x0) / setup.hx, (Ys - y0) / setup.hy, Ps
+
+
+def remap_2d(setup, phi, ex, ey, o):
+    """2D remap, eq. 5.4: solve H(xi*, eta*) phihat = phi* with the dense n^2 x n^2 matrix
+    H_{(ij),(lm)} = h_l(xi*_ij) h_m(eta*_ij), by Gaussian elimination (LAPACK gesv)."""
+    n, xi, _, _, _ = _elem_nodes_2d(setup, ex, ey)
+    xs, ys, ps = _advected_2d(setup, phi, ex, ey, o)
+    Lx = lagrange(xi, xs)            # (n^2, n) over l (x index)
+    Ly = lagrange(xi, ys)            # (n^2, n) over m (y index)
+    # unknown ordering (m, l) -> m * n + l, matching phi_e[j, i] with j = m (y), i = l (x)
+    H = (Ly[:, :, None] * Lx[:, None, :]).reshape(n * n, n * n)
+    return np.linalg.solve(H, ps).reshape(n, n)
+
+
+def poly_2d(setup, coef, ex, ey, xq, yq):
+    """Evaluate element (ex, ey)'s nodal polynomial (eq. 5.1) at physical points."""
+    n, xi, _, x0, y0 = _elem_nodes_2d(setup, ex, ey)
+    Lx = lagrange(xi, (np.atleast_1d(xq) - x0) / setup.hx)
+    Ly = lagrange(xi, (np.atleast_1d(yq) - y0) / setup.hy)
+    return np.einsum("qm,ml,ql->q", Ly, coef, Lx)
+
+
+def _nb_2d(setup, ex, ey, face):
+    """Neighbour across face 0=W, 1=E, 2=S, 3=N, or None at a non-periodic boundary."""
+    dx, dy = [(-1, 0), (1, 0), (0, -1), (0, 1)][face]
+    jx, jy = ex + dx, ey + dy
+    if 0 <= jx < setup.kx and 0 <= jy < setup.ky:
+        return jx, jy
+    if setup.bc[face] == BC_PERIODIC:
+        return jx % setup.kx, jy % setup.ky
+    return None
+
+
+def _face_points(setup, ex, ey, face, nq):
+    """Physical face points at the tangential Gauss nodes of an nq-point rule, outward
+    normal, and face quadrature weights (h_t * w)."""
+    xi, w = nodes_weights(nq, setup.basis)
+    x0 = setup.box[0] + ex * setup.hx
+    y0 = setup.box[2] + ey * setup.hy
+    if face in (0, 1):
+        xf = np.full(nq, x0 + (setup.hx if face == 1 else 0.0))
+        yf = y0 + setup.hy * xi
+        nrm = (1.0 if face == 1 else -1.0, 0.0)
+        W = setup.hy * w
+    else:
+        yf = np.full(nq, y0 + (setup.hy if face == 3 else 0.0))
+        xf = x0 + setup.hx * xi
+        nrm = (0.0, 1.0 if face == 3 else -1.0)
+        W = setup.hx * w
+    return xf, yf, nrm, W
+
+
+def _periodic_shift(setup, ex, ey, face, nb):
+    """Physical offset to add to a point of element (ex, ey) to express it in the frame of
+    neighbour ``nb`` (non-zero only across a periodic wrap)."""
+    dx, dy = [(-1, 0), (1, 0), (0, -1), (0, 1)][face]
+    return (nb[0] - (ex + dx)) * setup.hx, (nb[1] - (ey + dy)) * setup.hy
+
+
+def element_step_2d(setup, phi, ex, ey, o, phihat_cache=None):
+    """One DSEM-SL step for element (ex, ey) of a 2D mesh (Sec. 4, two-dimensional scheme).
+
+    Returns (phi_new (n, n), info)."""
+    cache = {} if phihat_cache is None else phihat_cache
+
+    def phihat_of(jx, jy):
+        key = (jx, jy)
+        if key not in cache:
+            cache[key] = remap_2d(setup, phi, jx, jy, o)
+        return cache[key]
+
+    n, xi, w, x0, y0 = _elem_nodes_2d(setup, ex, ey)
+    hx, hy = setup.hx, setup.hy
+    ph = phihat_of(ex, ey)
+    tn1 = o.t + o.dt
+    L0, L1 = lagrange(xi, [0.0])[0], lagrange(xi, [1.0])[0]
+    rows, rhs = [], []
+    if o.constraints & C_BOUNDARY:
+        for face in range(4):
+            xf, yf, nrm, _ = _face_points(setup, ex, ey, face, n)
+            u, v, _ = velocity(o.vel, xf, yf, tn1)
+            un = u * nrm[0] + v * nrm[1]
+            own = poly_2d(setup, ph, ex, ey, xf, yf)           # eq. 2dx/2dy_bnd_interpolate
+            nb = _nb_2d(setup, ex, ey, face)
+            if nb is None:
+                other = _ghost(setup, xf, yf, tn1)
+            else:
+                sx, sy = _periodic_shift(setup, ex, ey, face, nb)
+                other = poly_2d(setup, phihat_of(*nb), nb[0], nb[1], xf + sx, yf + sy)
+            for q in range(n):
+                # row: trace of the unknown polynomial at this face point
+                if face in (0, 1):
+                    Lt = L1 if face == 1 else L0
+                    row = np.zeros((n, n))
+                    row[q, :] = Lt                     # phi[j=q, i] * l_i(face)
+                else:
+                    Lt = L1 if face == 3 else L0
+                    row = np.zeros((n, n))
+                    row[:, q] = Lt                     # phi[j, i=q] * l_j(face)
+                if un[q] > TIE:
+                    val = own[q]
+                elif un[q] < -TIE:
+                    val = other[q]
+                else:
+                    val = own[q] if nb is None else 0.5 * (own[q] + other[q])
+                rows.append(row.ravel())
+                rhs.append(val)
+    W2 = hx * hy * np.outer(w, w)                          # h^d w o w, [j, i]
+    phin = _get(phi, ex, ey).astype(np.float64)
+    need_flux = o.constraints & (C_MASS | C_ENERGY)
+    Fm = Fe = 0.0
+    if need_flux:
+        _, b, c = rk_tableau(o.rk_order)
+        for face in range(4):
+            nb = _nb_2d(setup, ex, ey, face)
+            nq = n if nb is None else max(n, setup.n_of(*nb))   # R10
+            xf, yf, nrm, Wq = _face_points(setup, ex, ey, face, nq)
+            for s in range(len(b)):
+                tau = o.t + c[s] * o.dt
+                u, v, _ = velocity(o.vel, xf, yf, tau)
+                un = u * nrm[0] + v * nrm[1]
+                if c[s] == 0.0:
+                    fx, fy, fac = xf, yf, np.ones(nq)
+                else:
+                    fx, fy, fac = rk_particles(o.vel, xf, yf, np.ones(nq), tau, -c[s] * o.dt,
+                                               o.rk_order)
+                own = poly_2d(setup, phin, ex, ey, fx, fy) / fac
+                if nb is None:
+                    other = _ghost(setup, xf, yf, tau)
+                else:
+                    sx, sy = _periodic_shift(setup, ex, ey, face, nb)
+                    other = poly_2d(setup, _get(phi, *nb).astype(np.float64), nb[0], nb[1],
+                                    fx + sx, fy + sy) / fac
+                val = np.where(un > TIE, own, np.where(un < -TIE, other, 0.0))
+                unz = np.where(np.abs(un) <= TIE, 0.0, un)
+                Fm += b[s] * np.sum(Wq * unz * val)
+                Fe += b[s] * np.sum(Wq * unz * val ** 2)
+    if o.constraints & C_MASS:
+        rows.append(W2.ravel())
+        rhs.append(np.sum(W2 * phin) - o.dt * Fm)
+    C = np.array(rows).reshape(len(rows), n * n)
+    d = np.array(rhs, dtype=np.float64)
+    ew, Et = None, 0.0
+    if o.constraints & C_ENERGY:
+        ew, Et = W2.ravel(), np.sum(W2 * phin ** 2) - o.dt * Fe
+    tol = o.picard_tol if o.picard_tol is not None else PICARD_RTOL * max(np.max(np.abs(ph)), 1e-300)
+    new, iters, conv = constrained_fit(ph.ravel(), C, d, ew, Et, o.fit, tol, o.picard_cap)
+    return new.reshape(n, n), {"phihat": ph, "C": C, "d": d, "iters": iters, "converged": conv,
+                               "E_target": Et}
+
+
+def step_2d(setup, phi, o, elements=None):
+    """Advance a 2D state by one step.  ``phi`` is (ky, kx, n, n) for uniform n, or a nested
+    list [ey][ex] of (n_e, n_e) arrays.  ``elements`` = iterable of (ex, ey) to restrict."""
+    uniform = isinstance(phi, np.ndarray)
+    if uniform:
+        phi = np.asarray(phi, dtype=np.float64)
+        out = phi.copy()
+    else:
+        out = [[np.array(e, dtype=np.float64) for e in row] for row in phi]
+    cache = {}
+    infos = {}
+    todo = [(ex, ey) for ey in range(setup.ky) for ex in range(setup.kx)] if elements is None else elements
+    for ex, ey in todo:
+        new, info = element_step_2d(setup, phi, int(ex), int(ey), o, cache)
+        if uniform:
+            out[ey, ex] = new
+        else:
+            out[ey][ex] = new
+        infos[(int(ex), int(ey))] = info
+    return out, infos
+
+
+# ============================================================================ state setup & norms
+
+
+def node_coords_1d(setup):
+    """Physical node positions (K, n)."""
+    xi, _ = nodes_weights(setup.n, setup.basis)
+    k = np.arange(setup.kx)[:, None]
+    return setup.box[0] + (k + xi[None, :]) * setup.hx
+
+
+def node_coords_2d(setup, ex, ey):
+    n, xi, _, x0, y0 = _elem_nodes_2d(setup, ex, ey)
+    X = x0 + setup.hx * np.broadcast_to(xi[None, :], (n, n))
+    Y = y0 + setup.hy * np.broadcast_to(xi[:, None], (n, n))
+    return X, Y
+
+
+def project_1d(setup, f):
+    return f(node_coords_1d(setup))
+
+
+def project_2d(setup, f):
+    if setup.orders is None:
+        out = np.empty((setup.ky, setup.kx, setup.n, setup.n))
+        for ey in range(setup.ky):
+            for ex in range(setup.kx):
+                X, Y = node_coords_2d(setup, ex, ey)
+                out[ey, ex] = f(X, Y)
+        return out
+    return [[f(*node_coords_2d(setup, ex, ey)) for ex in range(setup.kx)] for ey in range(setup.ky)]
+
+
+def quad_weights(setup, ex=0, ey=0):
+    """Physical quadrature weights of one element: h w (1D) or hx hy w o w (2D)."""
+    n = setup.n_of(ex, ey)
+    _, w = nodes_weights(n, setup.basis)
+    if setup.dim == 1:
+        return setup.hx * w
+    return setup.hx * setup.hy * np.outer(w, w)
+
+
+def _iter_elems(setup, phi):
+    if setup.dim == 1:
+        for k in range(setup.kx):
+            yield quad_weights(setup), np.asarray(phi[k], dtype=np.float64)
+    else:
+        for ey in range(setup.ky):
+            for ex in range(setup.kx):
+                yield quad_weights(setup, ex, ey), np.asarray(_get(phi, ex, ey), dtype=np.float64)
+
+
+def mass(setup, phi):
+    """Global mass sum_k integral phi (eq. quad summed over elements)."""
+    return float(sum(np.sum(W * p) for W, p in _iter_elems(setup, phi)))
+
+
+def energy(setup, phi):
+    """Global energy sum_k integral phi^2."""
+    return float(sum(np.sum(W * p * p) for W, p in _iter_elems(setup, phi)))
+
+
+def rel_l2(setup, a, b):
+    """Quadrature-weighted relative L2 difference sqrt(sum W (a-b)^2) / sqrt(sum W b^2)."""
+    num = den = 0.0
+    for (W, pa), (_, pb) in zip(_iter_elems(setup, a), _iter_elems(setup, b)):
+        num += np.sum(W * (pa - pb) ** 2)
+        den += np.sum(W * pb ** 2)
+    return math.sqrt(num / den) if den > 0 else math.sqrt(num)
+
+
+def paper_error_norm(setup, phi, exact_fn, reference_measure=False):
+    """Eq. 5.2: sum over elements of sqrt(integral_k (phi - phi_exact)^2), by the element's
+    Gauss rule; ``reference_measure`` integrates in d xi instead of dx."""
+    total = 0.0
+    if setup.dim == 1:
+        X = node_coords_1d(setup)
+        _, w = nodes_weights(setup.n, setup.basis)
+        for k in range(setup.kx):
+            wk = w if reference_measure else setup.hx * w
+            total += math.sqrt(np.sum(wk * (phi[k] - exact_fn(X[k])) ** 2))
+        return total
+    for ey in range(setup.ky):
+        for ex in range(setup.kx):
+            X, Y = node_coords_2d(setup, ex, ey)
+            _, w = nodes_weights(setup.n_of(ex, ey), setup.basis)
+            W = np.outer(w, w) if reference_measure else setup.hx * setup.hy * np.outer(w, w)
+            total += math.sqrt(np.sum(W * (_get(phi, ex, ey) - exact_fn(X, Y)) ** 2))
+    return total

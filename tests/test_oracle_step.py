@@ -1,0 +1,286 @@
+"""Pins of the oracle's whole step against what the paper and the mathematics fix: exact
+translation of polynomial data, the 1D remap identity (eq. 4.9 = collocation solve), the 2D
+Kronecker collocation, constraint satisfaction, mass and energy telescoping, upwind locality,
+exponential convergence in N, and the period-two cycle of the paper's literal energy iteration."""
+import numpy as np
+import pytest
+
+from oracle import sl_oracle as O
+
+CONST = O.Vel(O.VEL_CONST, (0.8, 0.45, 0, 0, 0, 0))
+
+
+def poly1(x):
+    return 0.3 + x - 2.0 * x ** 2 + 1.5 * x ** 3
+
+
+def poly2(x, y):
+    return 0.2 + x - 0.7 * y + 1.3 * x * y - 0.5 * x * x * y + 0.8 * y ** 3
+
+
+def _ghost_exact_1d(f, a):
+    return lambda x, y, t: f(np.asarray(x) - a * t)
+
+
+@pytest.mark.parametrize("fit", [O.FIT_HARD, O.FIT_SOFT])
+@pytest.mark.parametrize("n", [4, 6, 9])
+@pytest.mark.parametrize("basis", [O.GAUSS_LEGENDRE, O.CHEB_GAUSS])
+def test_1d_exact_translation_boundary(fit, n, basis):
+    """Constant velocity, boundary constraints, inflow ghost = the exact solution, polynomial
+    data of degree <= N: one step equals the exact translate to round-off (Sec. 5.1)."""
+    a = 0.8
+    s = O.Setup(1, 5, 1, (0.0, 1.0, 0, 0), n, basis, (O.BC_INFLOW,) * 4, _ghost_exact_1d(poly1, a))
+    phi = O.project_1d(s, poly1)
+    dt = O.max_dt(s, CONST)
+    o = O.StepOpts(CONST, 0.1, dt, O.C_BOUNDARY, 4, fit)
+    out, _ = O.step_1d(s, phi, o)
+    # ghost is evaluated as f(x - a t): the state at t=0.1 is poly1 shifted by a*0.1
+    s2 = O.Setup(1, 5, 1, (0.0, 1.0, 0, 0), n, basis, (O.BC_INFLOW,) * 4, _ghost_exact_1d(poly1, a))
+    exact = O.project_1d(s2, lambda x: poly1(x - a * dt))
+    # data at t=0.1 must match the ghost's time: use ghost(x, t) = f(x - a (t - 0.1))
+    s.ghost = lambda x, y, t: poly1(np.asarray(x) - a * (t - 0.1))
+    out, _ = O.step_1d(s, phi, o)
+    np.testing.assert_allclose(out, exact, atol=1e-12)
+
+
+@pytest.mark.parametrize("cons", [O.C_BOUNDARY | O.C_MASS, O.C_MASS])
+@pytest.mark.parametrize("rk", [3, 4])
+def test_1d_exact_translation_mass(cons, rk):
+    """With the mass constraint the face flux is integrated by the RK quadrature, exact for
+    cubic-in-time integrands (Simpson): cubic data stays exactly translated (R5)."""
+    a, n = 0.8, 4
+    s = O.Setup(1, 4, 1, (0.0, 1.0, 0, 0), n, O.GAUSS_LEGENDRE, (O.BC_INFLOW,) * 4,
+                lambda x, y, t: poly1(np.asarray(x) - a * t))
+    phi = O.project_1d(s, poly1)
+    dt = O.max_dt(s, CONST)
+    out, _ = O.step_1d(s, phi, O.StepOpts(CONST, 0.0, dt, cons, rk))
+    exact = O.project_1d(s, lambda x: poly1(x - a * dt))
+    np.testing.assert_allclose(out, exact, atol=1e-12)
+
+
+def test_1d_exact_translation_energy_linear():
+    """Linear data: the energy flux phi^2 is quadratic in time, integrated exactly; the
+    energy-constrained fit keeps the exact translate."""
+    a, n = 0.8, 5
+    f = lambda x: 0.5 + 2.0 * x
+    s = O.Setup(1, 4, 1, (0.0, 1.0, 0, 0), n, O.GAUSS_LEGENDRE, (O.BC_INFLOW,) * 4,
+                lambda x, y, t: f(np.asarray(x) - a * t))
+    phi = O.project_1d(s, f)
+    dt = O.max_dt(s, CONST)
+    out, inf = O.step_1d(s, phi, O.StepOpts(CONST, 0.0, dt, O.C_BOUNDARY | O.C_MASS | O.C_ENERGY, 4))
+    exact = O.project_1d(s, lambda x: f(x - a * dt))
+    np.testing.assert_allclose(out, exact, atol=1e-12)
+    assert all(i["converged"] for i in inf.values())
+
+
+def test_1d_mass_sign():
+    """Inflow adds mass: uniform data 0 with ghost 1 entering from the left gains exactly
+    dt * u * 1 of mass in element 0 (reading R5 of the sign)."""
+    s = O.Setup(1, 3, 1, (0.0, 1.0, 0, 0), 5, O.GAUSS_LEGENDRE, (O.BC_INFLOW, O.BC_INFLOW, 0, 0), 1.0)
+    phi = np.zeros((3, 5))
+    dt = O.max_dt(s, CONST)
+    out, inf = O.step_1d(s, phi, O.StepOpts(CONST, 0.0, dt, O.C_MASS, 4))
+    m0 = np.dot(O.quad_weights(s), out[0])
+    assert abs(m0 - 0.8 * dt) < 1e-15
+
+
+def test_1d_remap_equals_collocation_solve():
+    """Eq. 4.9 (interpolation through advected nodes) equals solving the collocation system
+    of eq. 5.4 written in 1D."""
+    rng = np.random.default_rng(3)
+    for n in (3, 7, 12):
+        xi, _ = O.nodes_weights(n, O.GAUSS_LEGENDRE)
+        xs = xi + rng.uniform(-0.02, 0.02, n)
+        ps = rng.uniform(-1, 1, n)
+        via_interp = O.lagrange(xs, xi) @ ps
+        via_solve = np.linalg.solve(O.lagrange(xi, xs), ps)
+        np.testing.assert_allclose(via_interp, via_solve, atol=1e-13)
+
+
+def test_2d_remap_constant_velocity_is_kronecker():
+    """With constant velocity the 2D collocation matrix is A_y (x) A_x, so the remap equals
+    applying the 1D remap along x then along y."""
+    n = 6
+    s = O.Setup(2, 3, 3, (0, 1, 0, 1), n)
+    phi = O.random_state = np.random.default_rng(5).uniform(-1, 1, (3, 3, n, n))
+    dt = O.max_dt(s, CONST)
+    o = O.StepOpts(CONST, 0.0, dt)
+    ph = O.remap_2d(s, phi, 1, 2, o)
+    xi, _ = O.nodes_weights(n, O.GAUSS_LEGENDRE)
+    Rx = O.lagrange(xi + 0.8 * dt / s.hx, xi)
+    Ry = O.lagrange(xi + 0.45 * dt / s.hy, xi)
+    np.testing.assert_allclose(ph, Ry @ phi[2, 1] @ Rx.T, atol=1e-12)
+
+
+@pytest.mark.parametrize("fit", [O.FIT_HARD, O.FIT_SOFT])
+def test_2d_exact_translation(fit):
+    """2D constant velocity (u != v), boundary on four faces, exact inflow ghost, data of
+    degree <= N per direction: the step is the exact translate (Sec. 5.3)."""
+    n = 5
+    a, b = 0.8, 0.45
+    s = O.Setup(2, 3, 3, (0, 1, 0, 1), n, O.GAUSS_LEGENDRE, (O.BC_INFLOW,) * 4,
+                lambda x, y, t: poly2(np.asarray(x) - a * t, np.asarray(y) - b * t))
+    phi = O.project_2d(s, poly2)
+    dt = O.max_dt(s, CONST)
+    out, _ = O.step_2d(s, phi, O.StepOpts(CONST, 0.0, dt, O.C_BOUNDARY | O.C_MASS, 4, fit))
+    exact = O.project_2d(s, lambda x, y: poly2(x - a * dt, y - b * dt))
+    np.testing.assert_allclose(out, exact, atol=1e-12)
+
+
+def test_1d_constraints_hold_to_roundoff():
+    rng = np.random.default_rng(11)
+    s = O.Setup(1, 6, 1, (0, 1, 0, 0), 7)
+    phi = rng.uniform(-1, 1, (6, 7))
+    dt = O.max_dt(s, CONST)
+    _, inf = O.step_1d(s, phi, O.StepOpts(CONST, 0.0, dt, O.C_BOUNDARY | O.C_MASS, 4))
+    out, _ = O.step_1d(s, phi, O.StepOpts(CONST, 0.0, dt, O.C_BOUNDARY | O.C_MASS, 4))
+    for k, i in inf.items():
+        r = i["C"] @ out[k] - i["d"]
+        assert np.max(np.abs(r)) <= 1e-13 * max(1.0, np.max(np.abs(i["d"])))
+
+
+def test_2d_constraints_pseudo_inverse_and_rank():
+    """Four faces of boundary rows have rank 4n-4 (one dependency per corner); the hard fit
+    meets C phi = C C^+ d, with C^+ from an SVD (numpy pinv), not the oracle's QR path."""
+    rng = np.random.default_rng(12)
+    n = 5
+    s = O.Setup(2, 3, 3, (0, 1, 0, 1), n)
+    phi = rng.uniform(-1, 1, (3, 3, n, n))
+    dt = O.max_dt(s, CONST)
+    out, inf = O.step_2d(s, phi, O.StepOpts(CONST, 0.0, dt, O.C_BOUNDARY | O.C_MASS, 4),
+                         elements=[(1, 1)])
+    C, d = inf[(1, 1)]["C"], inf[(1, 1)]["d"]
+    assert np.linalg.matrix_rank(C[: 4 * n]) == 4 * n - 4
+    assert np.linalg.matrix_rank(C) == 4 * n - 3
+    np.testing.assert_allclose(C @ out[1, 1].ravel(), C @ np.linalg.pinv(C) @ d, atol=1e-12)
+    ph = inf[(1, 1)]["phihat"].ravel()
+    ref = ph + np.linalg.pinv(C) @ (d - C @ ph)
+    np.testing.assert_allclose(out[1, 1].ravel(), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("rk", [1, 2, 4])
+def test_1d_periodic_mass_energy_telescoping(rk):
+    """Unique upwind face fluxes telescope: with MASS (and ENERGY) constraints the periodic
+    global mass (and energy) is constant to round-off.  First-order fluxes make some energy
+    targets unreachable (the paper's MEF1 instability), so RK1 checks mass only."""
+    rng = np.random.default_rng(rk)
+    s = O.Setup(1, 8, 1, (0, 1, 0, 0), 6)
+    phi = O.project_1d(s, lambda x: np.sin(2 * np.pi * x) + 0.1 * np.cos(6 * np.pi * x) + 0.5)
+    phi = phi + 1e-3 * rng.uniform(-1, 1, phi.shape)
+    dt = O.max_dt(s, CONST)
+    cons = O.C_BOUNDARY | O.C_MASS | (O.C_ENERGY if rk > 1 else 0)
+    o = O.StepOpts(CONST, 0.0, dt, cons, rk)
+    m0, e0 = O.mass(s, phi), O.energy(s, phi)
+    for _ in range(5):
+        phi, inf = O.step_1d(s, phi, o)
+        assert all(i["converged"] for i in inf.values())
+        o.t += o.dt
+    assert abs(O.mass(s, phi) - m0) < 1e-13 * abs(m0)
+    if cons & O.C_ENERGY:
+        assert abs(O.energy(s, phi) - e0) < 1e-13 * abs(e0)
+
+
+def test_2d_periodic_mass_telescoping_rotation_like():
+    s = O.Setup(2, 4, 4, (0, 1, 0, 1), 5)
+    vel = O.Vel(O.VEL_SWIRL, (5.0, 0, 0, 0, 0, 0))
+    phi = O.project_2d(s, lambda x, y: 1.0 + np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y))
+    dt = O.max_dt(s, vel)
+    o = O.StepOpts(vel, 0.3, dt, O.C_BOUNDARY | O.C_MASS | O.C_ENERGY, 4)
+    m0, e0 = O.mass(s, phi), O.energy(s, phi)
+    out, inf = O.step_2d(s, phi, o)
+    assert all(i["converged"] for i in inf.values())
+    assert abs(O.mass(s, out) - m0) < 1e-13 * abs(m0)
+    assert abs(O.energy(s, out) - e0) < 1e-13 * abs(e0)
+
+
+def test_1d_upwind_locality():
+    """Information moves downstream only: with u > 0 a change in element k alters the step
+    result of elements k and k+1, never k-1 (upwinding, eq. 4.12a)."""
+    rng = np.random.default_rng(4)
+    s = O.Setup(1, 7, 1, (0, 1, 0, 0), 6)
+    phi = rng.uniform(-1, 1, (7, 6))
+    dt = O.max_dt(s, CONST)
+    o = O.StepOpts(CONST, 0.0, dt, O.C_BOUNDARY | O.C_MASS, 4)
+    base, _ = O.step_1d(s, phi, o)
+    pert = phi.copy()
+    pert[3] += rng.uniform(-1, 1, 6)
+    out, _ = O.step_1d(s, pert, o)
+    changed = np.max(np.abs(out - base), axis=1) > 1e-14
+    assert changed.tolist() == [False, False, False, True, True, False, False]
+
+
+def test_2d_upwind_locality():
+    rng = np.random.default_rng(6)
+    n = 4
+    s = O.Setup(2, 4, 4, (0, 1, 0, 1), n)
+    phi = rng.uniform(-1, 1, (4, 4, n, n))
+    dt = O.max_dt(s, CONST)
+    o = O.StepOpts(CONST, 0.0, dt, O.C_BOUNDARY | O.C_MASS, 4)
+    base, _ = O.step_2d(s, phi, o)
+    pert = phi.copy()
+    pert[1, 1] += 1.0
+    out, _ = O.step_2d(s, pert, o)
+    changed = np.max(np.abs(out - base), axis=(2, 3)) > 1e-14
+    expect = np.zeros((4, 4), bool)
+    expect[1, 1] = expect[1, 2] = expect[2, 1] = True      # self, east and north (u, v > 0)
+    assert (changed == expect).all()
+
+
+def test_exponential_convergence_in_n():
+    """Sec. 5.1: errors after a fixed time fall exponentially with the polynomial order."""
+    errs = []
+    for n in (3, 5, 7, 9):
+        s = O.Setup(1, 4, 1, (0, 1, 0, 0), n)
+        v = O.Vel(O.VEL_CONST, (1.0, 0, 0, 0, 0, 0))
+        phi = O.project_1d(s, lambda x: np.sin(2 * np.pi * x))
+        dt = 0.25 / 30
+        o = O.StepOpts(v, 0.0, dt, O.C_BOUNDARY, 4)
+        for _ in range(30):
+            phi, _ = O.step_1d(s, phi, o)
+            o.t += dt
+        errs.append(O.rel_l2(s, phi, O.project_1d(s, lambda x: np.sin(2 * np.pi * (x - 0.25)))))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(r > 20 for r in ratios), (errs, ratios)
+
+
+def test_literal_picard_cycles_hard_fit_converges():
+    """Reading R7: the paper's linearised energy row gives phi_k = c / phi_{k-1} in the
+    scalar case (period two); the hard fit's iteration lands on sqrt(c)."""
+    C = np.zeros((0, 1))
+    d = np.zeros(0)
+    wgt = np.array([1.0])
+    c = 2.0
+    x = np.array([1.0])
+    seq = []
+    for _ in range(6):                      # the literal iteration
+        x = O.fit_hard(np.array([1.0]), np.vstack([C, wgt * x]), np.array([c]))
+        seq.append(float(x[0]))
+    assert abs(seq[0] - 2.0) < 1e-15 and abs(seq[1] - 1.0) < 1e-15 and abs(seq[2] - 2.0) < 1e-15
+    phi, it, conv = O.constrained_fit(np.array([1.0]), C, d, wgt, c, O.FIT_HARD, 1e-14, 60)
+    assert conv and abs(phi[0] - np.sqrt(2.0)) < 1e-14 and it <= 3
+
+
+def test_energy_fixed_point_is_kkt_point():
+    """The converged energy fit is a stationary point of min |phi - phihat| subject to the
+    linear rows and the exact energy: phi - phihat lies in span(C^T, W o phi)."""
+    rng = np.random.default_rng(9)
+    n = 7
+    xi, w = O.nodes_weights(n, O.GAUSS_LEGENDRE)
+    C = np.vstack([O.lagrange(xi, [0.0, 1.0]), w])
+    ph = np.sin(3 * xi) + 0.01 * rng.uniform(-1, 1, n)
+    d = C @ ph + 0.01 * rng.uniform(-1, 1, 3)
+    E = 1.02 * np.dot(w, ph * ph)
+    phi, it, conv = O.constrained_fit(ph, C, d, w, E, O.FIT_HARD, 1e-15, 60)
+    assert conv and it < 20
+    assert abs(np.dot(w, phi * phi) - E) < 1e-14
+    np.testing.assert_allclose(C @ phi, d, atol=1e-14)
+    basis = np.vstack([C, w * phi]).T
+    coef, *_ = np.linalg.lstsq(basis, phi - ph, rcond=None)
+    assert np.max(np.abs(basis @ coef - (phi - ph))) < 1e-13
+
+
+def test_cfl_keeps_displacement_below_one_element():
+    for n in (5, 9, 13, 17):
+        s = O.Setup(1, 16, 1, (0, 1, 0, 0), n)
+        dt = O.max_dt(s, CONST)
+        assert 0.8 * dt < s.hx
