@@ -1,0 +1,292 @@
+"""Benchmark of the DSEM-SL step on GB300: Gauss-node updates per second.
+
+Workload: 1D linear advection at constant speed a = 1 on the periodic unit interval,
+K = 2^20 elements, N = 8 (9 Gauss-Legendre nodes), Gaussian pulse, boundary + mass + energy
+constraints, RK4 particle integration, dt = half the minimum node spacing.  One bench step is
+one time step of the whole mesh.  Inputs stay resident in HBM; L2 (129 MB) is flushed by
+writing a 256 MB buffer before every timed step.
+
+``python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]``
+Under torchrun each rank runs an independent replica (independent problems; no collective).
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import math
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sl_inputs  # noqa: E402
+
+METRIC = "Gauss-node updates/sec per time step at stated L2 error vs FP64; % HBM roofline"
+UNIT = "node-updates/s"
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    try:
+        d = json.load(open(MEASURED))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload_config(n, precision_name):
+    return {"workload": f"1d_const_advection_K2^20_N{n - 1}_n{n}_GL_boundary+mass+energy_RK4_{precision_name}",
+            "elements": 1 << 20, "nodes_per_element": n, "steps_per_bench_step": 1,
+            "l2_flush": "256MB write before every timed step", "parallelism": "replicas"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = [r.split(",") for r in open(self.file.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n, seconds=12.0, cons=7):
+    """The FP64 oracle as it stands, on a bounded sample of elements of the same workload."""
+    from oracle import sl_oracle as O
+    prob = sl_inputs.config2_1d_gauss(n)
+    setup = O.setup_from_problem(prob)
+    phi = O.project_1d(setup, prob.phi0)
+    vel = O.Vel(O.VEL_CONST, (1.0, 0, 0, 0, 0, 0))
+    o = O.StepOpts(vel, 0.0, O.max_dt(setup, vel), cons, 4)
+    # elements across the pulse, where every term of the step is active
+    centre = prob.kx // 2
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        ks = range(centre + done, centre + done + 64)
+        O.step_1d(setup, phi, o, elements=ks)
+        done += 64
+    el = time.perf_counter() - t0
+    return {"value": done * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} elements (x{n} nodes) of one step at the pulse centre, {el:.1f} s, numpy FP64, 1 thread"}
+
+
+def run_reference(args, rank, world):
+    n = args.n
+    if rank != 0:
+        return
+    per = []
+    # each step is a bounded sample so that the whole run stays within about two minutes
+    sec = max(0.2, min(args.ref_seconds, 90.0 / (args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(n, seconds=min(sec, 0.5))
+    for _ in range(args.steps):
+        per.append(cpu_baseline(n, seconds=sec))
+    vals = [p["value"] for p in per]
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * (1 << 20) * n / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(n, "fp64_oracle_cpu"),
+            "cpu_baseline": dict(per[-1], value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1910_06476_gb300 as sl
+    from paper_1910_06476_gb300 import build as B
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    n = args.n
+    prob = sl_inputs.config2_1d_gauss(n)
+    precision = sl.FP64
+    stream = torch.cuda.current_stream()
+    ctx = sl.Context(1, prob.kx, 1, prob.box, n, sl.GAUSS_LEGENDRE, precision, prob.bc, prob.ghost, stream)
+    vel = sl.velocity(sl.VEL_CONST, 1.0)
+    dt = ctx.max_dt(vel)
+    opts = sl.options(prob.constraints, 4)
+    x, _ = ctx.node_coords()
+    phi0 = prob.phi0(x)
+    a = torch.tensor(phi0, device="cuda", dtype=ctx.dtype)
+    b = torch.empty_like(a)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    t = 0.0
+    for _ in range(args.warmup):
+        ctx.step(a, b, vel, t, dt, opts)
+        a, b = b, a
+        t += dt
+    torch.cuda.synchronize()
+    assert ctx.sync() == 0, "device status bits set during warm-up"
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        for s in range(args.steps):
+            flush.zero_()
+            starts[s].record(stream)
+            ctx.step(a, b, vel, t, dt, opts)
+            ends[s].record(stream)
+            a, b = b, a
+            t += dt
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    status = ctx.sync()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    nodes = prob.kx * n
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * nodes * args.steps / (total_ms * 1e-3)
+
+    # end to end: host buffers in, one step, host buffer out (sl_run_host), every step
+    e2e_steps = min(args.steps, 50)
+    host_in = torch.tensor(phi0, dtype=ctx.dtype).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ctx.run_host(host_in, host_out, vel, 0.0, dt, 1, opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        ctx.run_host(host_in, host_out, vel, s * dt, dt, 1, opts)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * nodes * e2e_steps / e2e_s
+    state_bytes = nodes * (8 if precision == sl.FP64 else 4)
+
+    # accuracy: sampled one-step parity against the FP64 oracle from the GPU's own state
+    err = None
+    if rank == 0 and not args.no_check:
+        from oracle import sl_oracle as O
+        setup = O.setup_from_problem(prob)
+        pre = a.double().cpu().numpy()
+        ctx.step(a, b, vel, t, dt, opts)
+        got = b.double().cpu().numpy()
+        sample = np.unique(np.concatenate([sl_inputs.sample_elements(64, prob.kx, 5),
+                                           np.arange(prob.kx // 2 - 32, prob.kx // 2 + 32)]))
+        ref, _ = O.step_1d(setup, pre, O.StepOpts(O.Vel(O.VEL_CONST, (1.0, 0, 0, 0, 0, 0)), t, dt,
+                                                  prob.constraints, 4), elements=sample)
+        num = np.sqrt(np.sum((got[sample] - ref[sample]) ** 2))
+        den = np.sqrt(np.sum(ref[sample] ** 2))
+        err = float(num / den)
+
+    if rank != 0:
+        return
+    hbm, peak_kind = peaks()
+    bytes_per_node = 2 * (8 if precision == sl.FP64 else 4)
+    avg_ms = total_ms / args.steps
+    achieved = nodes * bytes_per_node / (avg_ms * 1e-3) / 1e9
+    clk = clocks.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if precision == sl.FP64 else "f32",
+            "data": "synthetic (seeded analytic Gaussian pulse)", "config": workload_config(n, "fp64_per_element"),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_node": bytes_per_node,
+                         "kernel": "k_step1d_f64"},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "gpu_launches": args.steps,
+            "l2_error_vs_fp64_oracle": {"after_1_step_sampled": err},
+            "device_status": status}
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(n, seconds=args.ref_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=9, help="nodes per element (N + 1)")
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * sl.h -- C ABI of the GB300 library for the explicit semi-Lagrangian spectral (DSEM-SL)
+ * transport step of Natarajan & Jacobs, "An explicit semi-Lagrangian, spectral method for
+ * solution of Lagrangian transport equations in Eulerian-Lagrangian formulations"
+ * (arXiv:1910.06476).
+ *
+ * One call of sl_step advances every element of a mesh by one time step (Sec. 4):
+ *   (a) particles are seeded at the element's Gauss nodes (Sec. 4.1, eq. gaussquad, 4.2);
+ *   (b) they are integrated explicitly through the velocity field together with the value
+ *       equation D phi / Dt = -phi div u (Sec. 4.2, eq. 4.4a, 4.8; eq. 2.4, 2.5);
+ *   (c) the advected polynomial is remapped to the Gauss nodes (eq. 4.9 in 1D, the
+ *       collocation system eq. 5.4 in 2D) and its face traces are taken (eq. remap_bnd,
+ *       2dx_bnd_interpolate, 2dy_bnd_interpolate);
+ *   (d) a least-squares fit constrained by upwinded interface values (eq. 4.12a) and
+ *       optionally by local mass and energy (eq. 4.14, quad, remap_mass, remap_energy)
+ *       yields phi^{n+1} (eq. matrix_a).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named phi* are DEVICE pointers to the state, owned by the caller.  State
+ *     layout: 1D [K][n]; 2D [ky][kx][n][n] with the x index fastest (node (i, j) of element
+ *     (ex, ey) at offset ((ey*kx + ex)*n + j)*n + i); p-adaptive 2D meshes store element e
+ *     (row-major over (ey, ex)) at offset off[e] with n_e*n_e values, off being the exclusive
+ *     prefix sum of n_e^2.  Element type: double for SL_FP64, float for SL_MIXED.
+ *   - Pointers documented as "host" are host memory; everything else is device memory.
+ *   - The library owns its tables, operators and workspace (allocated in sl_init and freed in
+ *     sl_free).  All device work is enqueued on the stream given to sl_init; no call
+ *     synchronises the stream except sl_mass, sl_energy, sl_sync and sl_run_host, which
+ *     return host values.
+ *   - Every function returns an sl_status.  Argument errors are reported before any work is
+ *     enqueued and leave the state untouched; sl_last_error gives a one-line reason.  Errors
+ *     found on the device (non-finite values, an energy iteration that hit its cap, a
+ *     collocation solve that did not converge) are sticky bits read by sl_sync.  Nothing in
+ *     the library aborts the process.
+ */
+#ifndef SL_H
+#define SL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sl_ctx sl_ctx;
+
+typedef enum {
+  SL_OK = 0,
+  SL_EINVAL = 1,       /* bad argument (null pointer, size, enum value)                  */
+  SL_ENOMEM = 2,       /* device allocation failed                                       */
+  SL_ECUDA = 3,        /* a CUDA runtime call failed                                     */
+  SL_ECFL = 4,         /* displacement over one step would exceed one element width      */
+  SL_EDEVICE = 5,      /* device status bits are set (see sl_sync)                       */
+  SL_EUNSUPPORTED = 6  /* valid request that this build does not implement               */
+} sl_status;
+
+/* Solution node families (Sec. 3, eq. gaussquad): Gauss-Legendre, or Chebyshev-Gauss
+ * xi_i = (1 - cos((i + 1/2) pi / n)) / 2.  Quadrature weights (eq. quad) are the Gauss
+ * weights, or for Chebyshev-Gauss nodes the interpolatory (Fejer first-rule) weights. */
+enum { SL_GAUSS_LEGENDRE = 0, SL_CHEB_GAUSS = 1 };
+
+/* Arithmetic: SL_FP64 computes every step in double precision on double state.
+ * SL_MIXED keeps float state and float bulk arithmetic, with the constraint integrals and
+ * the scalars of the energy iteration carried to double-precision accuracy. */
+enum { SL_FP64 = 0, SL_MIXED = 1 };
+
+/* Domain faces: periodic wrap, or an inflow face that sees the constant ghost value
+ * (Sec. 4.3: boundary conditions through a specified ghost solution). */
+enum { SL_BC_PERIODIC = 0, SL_BC_INFLOW = 1 };
+
+/* Prescribed velocity fields (Sec. 4.2: velocity taken as prescribed).
+ *   SL_VEL_CONST    p = {a, b}: constant (Sec. 5.1, 5.3)
+ *   SL_VEL_ROTATION p = {omega, cx, cy}: u = -omega (y - cy), v = omega (x - cx)
+ *   SL_VEL_SWIRL    p = {T}: u = sin^2(pi x) sin(2 pi y) cos(pi t / T),
+ *                            v = -sin^2(pi y) sin(2 pi x) cos(pi t / T)
+ *   SL_VEL_SINX     u = -sin x, 1D only (Sec. 5.2, eq. usin_lagr) */
+enum { SL_VEL_CONST = 0, SL_VEL_ROTATION = 1, SL_VEL_SWIRL = 2, SL_VEL_SINX = 3 };
+
+/* Constraint rows of the least-squares fit (eq. matrix_a). */
+enum { SL_C_BOUNDARY = 1, SL_C_MASS = 2, SL_C_ENERGY = 4 };
+
+/* Fit: SL_FIT_HARD solves the lexicographic least-squares problem (constraints first, in the
+ * least-squares sense, then nearest to the remapped values); SL_FIT_SOFT solves the paper's
+ * stacked over-determined system (eq. matrix_a) by ordinary least squares. */
+enum { SL_FIT_HARD = 0, SL_FIT_SOFT = 1 };
+
+/* Interface values: SL_BV_INTERP evaluates the advected polynomial at the face
+ * (eq. remap_bnd); SL_BV_BACKTRACK evaluates phi^n at the backward foot (eq. 4.11). */
+enum { SL_BV_INTERP = 0, SL_BV_BACKTRACK = 1 };
+
+/* Time-step rules for sl_max_dt (eq. 1d_delt_condition, 2d_delt_condition). */
+enum { SL_RULE_HALF_MIN_SPACING = 0, SL_RULE_PAPER = 1 };
+
+/* Sticky device status bits (sl_sync). */
+enum {
+  SL_ST_NONFINITE = 1u,      /* a non-finite value was written                          */
+  SL_ST_PICARD_NOCONV = 2u,  /* the energy iteration hit its cap or was infeasible      */
+  SL_ST_SOLVE_NOCONV = 4u    /* the 2D collocation iteration hit its cap                */
+};
+
+typedef struct {
+  int dim;               /* 1 or 2                                                          */
+  int kx, ky;            /* elements per direction (ky = 1 in 1D)                           */
+  double x0, x1, y0, y1; /* domain box (y0, y1 ignored in 1D)                               */
+  int bc[4];             /* faces W, E, S, N (1D uses W, E)                                 */
+  double ghost;          /* value at inflow domain faces                                    */
+  const int32_t* order;  /* host, nullable: per-element node counts, [ky][kx] (p-adaptive) */
+} sl_mesh;
+
+typedef struct {
+  int kind;              /* SL_VEL_*                                                        */
+  double p[6];           /* parameters, see SL_VEL_*                                        */
+} sl_velocity;
+
+typedef struct {
+  unsigned constraints;  /* SL_C_* bits                                                     */
+  int rk_order;          /* 1 (Euler), 2 (Heun), 3 (Kutta), 4 (classical)                   */
+  int fit;               /* SL_FIT_HARD or SL_FIT_SOFT                                      */
+  int bvalue;            /* SL_BV_INTERP or SL_BV_BACKTRACK                                 */
+  double picard_rtol;    /* energy iteration stops when max|change| < rtol * max|phihat|;
+                            0 selects 1e-13                                                 */
+  int picard_cap;        /* iteration cap, 0 selects 60                                     */
+} sl_options;
+
+/* Create a context for one mesh.  n = nodes per direction (polynomial degree n - 1),
+ * 2 <= n <= 17 (ignored when mesh->order is given, whose entries must lie in [2, 17]).
+ * cuda_stream: a cudaStream_t (0 = legacy default stream).  Precomputes, in host double
+ * and long double arithmetic, the nodes, weights, face basis values and fit operators
+ * (Sec. 3, eq. 3.5, quad, matrix_a) and uploads them.  On success *out owns device memory
+ * until sl_free. */
+sl_status sl_init(const sl_mesh* mesh, int n, int basis, int precision, void* cuda_stream,
+                  sl_ctx** out);
+
+/* Release a context and its device memory.  Null is ignored. */
+void sl_free(sl_ctx* ctx);
+
+/* Advance the state by one step from time t to t + dt (Sec. 4, steps a-d).  phi_in and
+ * phi_out are distinct device buffers of sl_state_size values of the context's element
+ * type; phi_in is only read.  Returns SL_ECFL when |u|max dt exceeds the element width. */
+sl_status sl_step(sl_ctx* ctx, const void* phi_in, void* phi_out, const sl_velocity* vel,
+                  double t, double dt, const sl_options* opt);
+
+/* Advance nsteps steps from t0 with a fixed dt, starting from and ending in HOST buffers:
+ * copies host_in to the device, steps, copies the result to host_out, then synchronises.
+ * host_in and host_out hold sl_state_size values of the element type and may alias. */
+sl_status sl_run_host(sl_ctx* ctx, const void* host_in, void* host_out, const sl_velocity* vel,
+                      double t0, double dt, int nsteps, const sl_options* opt);
+
+/* Global mass sum_k integral phi and energy sum_k integral phi^2 (eq. quad summed over the
+ * elements, diagnostics of Sec. 5), accumulated in double in a fixed order (deterministic).
+ * *total is a host double; the call synchronises the stream. */
+sl_status sl_mass(sl_ctx* ctx, const void* phi, double* total);
+sl_status sl_energy(sl_ctx* ctx, const void* phi, double* total);
+
+/* Synchronise the stream, return and clear the sticky device status bits (SL_ST_*). */
+sl_status sl_sync(sl_ctx* ctx, uint32_t* status_bits);
+
+/* Largest dt allowed by a time-step rule for this mesh and velocity (host computation). */
+sl_status sl_max_dt(const sl_ctx* ctx, const sl_velocity* vel, int rule, double* dt);
+
+/* Number of node values of the state. */
+int64_t sl_state_size(const sl_ctx* ctx);
+
+/* Physical node coordinates in state layout, written to host arrays of sl_state_size
+ * doubles (y may be null in 1D), for setting up initial data. */
+sl_status sl_node_coords(const sl_ctx* ctx, double* x, double* y);
+
+/* Quadrature nodes and weights on [0, 1] of the context's basis for n nodes (host arrays). */
+sl_status sl_nodes_weights(const sl_ctx* ctx, int n, double* xi, double* w);
+
+/* Last error message of the context (or of the last failed sl_init when ctx is null). */
+const char* sl_last_error(const sl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SL_H */

@@ -19,6 +19,8 @@ in the design notes):
       w_i = integral_0^1 l_i (Fejer's first rule); for Gauss-Legendre they are the GL weights.
   R3  Particles are integrated in physical coordinates (eq. 4.4 writes u(xi)).
   R4  Each boundary-constraint row pairs with the upwinded value of the same face (matrix_a).
+      Mass and energy rows use the reference-measure weights w (eq. quad, M = sum w phi), so
+      their targets are the physical integrals divided by h^d.
   R5  Mass target: M^{n+1} = M^n - dt * (net outflow), i.e. inflow adds mass (eq. remap_mass
       vs matrix_a disagree in sign).  Over the step the face flux is integrated with the RK
       quadrature (b_s, c_s); the face value at stage time tau is the upwind element's phi^n
@@ -338,7 +340,7 @@ def energy_step_scalar(alpha, beta, gamma):
 def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode, tol, cap):
     """Least-squares remap with linear constraints and optional energy (Sec. 4.3, matrix_a).
 
-    ``energy_row_weights`` (h^d w o w, flattened) switches the energy constraint on; its row
+    ``energy_row_weights`` (w o w, flattened) switches the energy constraint on; its row
     is (weights o phi^(k-1)), iterated over k until max|phi^(k) - phi^(k-1)| < tol.
     Hard fit (reading R7): the correction direction of that row, q = P a^(k) with P the
     projector onto the null space of the linear rows, is taken from the previous iterate and
@@ -504,17 +506,18 @@ def element_step_1d(setup, phi, k, o):
             rows.append(Lb[side])
             rhs.append(_face_value_1d(setup, phi, k, side, o))
     if o.constraints & C_MASS:
+        # eq. quad / remap_mass in the reference measure: row w, target M^{n+1} / h
         Mn = h * np.dot(w, phi[k])
         F = _face_flux_1d(setup, phi, k, 0, o, 1) + _face_flux_1d(setup, phi, k, 1, o, 1)
-        rows.append(h * w)
-        rhs.append(Mn - o.dt * F)
+        rows.append(w)
+        rhs.append((Mn - o.dt * F) / h)
     C = np.array(rows).reshape(len(rows), xi.size)
     d = np.array(rhs, dtype=np.float64)
     ew, Et = None, 0.0
     if o.constraints & C_ENERGY:
         En = h * np.dot(w, phi[k] ** 2)
         F = _face_flux_1d(setup, phi, k, 0, o, 2) + _face_flux_1d(setup, phi, k, 1, o, 2)
-        ew, Et = h * w, En - o.dt * F
+        ew, Et = w, (En - o.dt * F) / h
     tol = o.picard_tol if o.picard_tol is not None else PICARD_RTOL * max(np.max(np.abs(phihat)), 1e-300)
     new, iters, conv = constrained_fit(phihat, C, d, ew, Et, o.fit, tol, o.picard_cap)
     return new, {"phihat": phihat, "C": C, "d": d, "iters": iters, "converged": conv,
@@ -693,14 +696,15 @@ def element_step_2d(setup, phi, ex, ey, o, phihat_cache=None):
                 unz = np.where(np.abs(un) <= TIE, 0.0, un)
                 Fm += b[s] * np.sum(Wq * unz * val)
                 Fe += b[s] * np.sum(Wq * unz * val ** 2)
+    w2 = np.outer(w, w)                                    # reference-measure weights
     if o.constraints & C_MASS:
-        rows.append(W2.ravel())
-        rhs.append(np.sum(W2 * phin) - o.dt * Fm)
+        rows.append(w2.ravel())
+        rhs.append((np.sum(W2 * phin) - o.dt * Fm) / (hx * hy))
     C = np.array(rows).reshape(len(rows), n * n)
     d = np.array(rhs, dtype=np.float64)
     ew, Et = None, 0.0
     if o.constraints & C_ENERGY:
-        ew, Et = W2.ravel(), np.sum(W2 * phin ** 2) - o.dt * Fe
+        ew, Et = w2.ravel(), (np.sum(W2 * phin ** 2) - o.dt * Fe) / (hx * hy)
     tol = o.picard_tol if o.picard_tol is not None else PICARD_RTOL * max(np.max(np.abs(ph)), 1e-300)
     new, iters, conv = constrained_fit(ph.ravel(), C, d, ew, Et, o.fit, tol, o.picard_cap)
     return new.reshape(n, n), {"phihat": ph, "C": C, "d": d, "iters": iters, "converged": conv,

@@ -1,0 +1,201 @@
+"""Thin ctypes binding of the DSEM-SL C ABI (include/sl.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.  PyTorch is
+used for device memory and streams.  The library must have been built
+(``paper_1910_06476_gb300.build.build()``); importing this module raises if it is missing."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsl.so")
+
+SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ECFL, SL_EDEVICE, SL_EUNSUPPORTED = range(7)
+GAUSS_LEGENDRE, CHEB_GAUSS = 0, 1
+FP64, MIXED = 0, 1
+BC_PERIODIC, BC_INFLOW = 0, 1
+VEL_CONST, VEL_ROTATION, VEL_SWIRL, VEL_SINX = 0, 1, 2, 3
+C_BOUNDARY, C_MASS, C_ENERGY = 1, 2, 4
+FIT_HARD, FIT_SOFT = 0, 1
+BV_INTERP, BV_BACKTRACK = 0, 1
+RULE_HALF_MIN_SPACING, RULE_PAPER = 0, 1
+ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV = 1, 2, 4
+
+EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run_host", "sl_mass", "sl_energy", "sl_sync",
+           "sl_max_dt", "sl_state_size", "sl_node_coords", "sl_nodes_weights", "sl_last_error"]
+
+
+class SlMesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("kx", C.c_int), ("ky", C.c_int),
+                ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("bc", C.c_int * 4), ("ghost", C.c_double), ("order", C.POINTER(C.c_int32))]
+
+
+class SlVelocity(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 6)]
+
+
+class SlOptions(C.Structure):
+    _fields_ = [("constraints", C.c_uint), ("rk_order", C.c_int), ("fit", C.c_int), ("bvalue", C.c_int),
+                ("picard_rtol", C.c_double), ("picard_cap", C.c_int)]
+
+
+class SlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"sl status {status}: {msg}")
+        self.status = status
+
+
+def load_library(path=LIB_PATH):
+    """Load libsl.so and declare every exported signature.  Raises if it was not built."""
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1910_06476_gb300.build.build() "
+                          "(the library has no CPU fallback)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.sl_init.argtypes = [C.POINTER(SlMesh), C.c_int, C.c_int, C.c_int, P, C.POINTER(P)]
+    lib.sl_free.argtypes = [P]
+    lib.sl_free.restype = None
+    lib.sl_step.argtypes = [P, P, P, C.POINTER(SlVelocity), C.c_double, C.c_double, C.POINTER(SlOptions)]
+    lib.sl_run_host.argtypes = [P, P, P, C.POINTER(SlVelocity), C.c_double, C.c_double, C.c_int,
+                                C.POINTER(SlOptions)]
+    lib.sl_mass.argtypes = [P, P, C.POINTER(C.c_double)]
+    lib.sl_energy.argtypes = [P, P, C.POINTER(C.c_double)]
+    lib.sl_sync.argtypes = [P, C.POINTER(C.c_uint32)]
+    lib.sl_max_dt.argtypes = [P, C.POINTER(SlVelocity), C.c_int, C.POINTER(C.c_double)]
+    lib.sl_state_size.argtypes = [P]
+    lib.sl_state_size.restype = C.c_int64
+    lib.sl_node_coords.argtypes = [P, P, P]
+    lib.sl_nodes_weights.argtypes = [P, C.c_int, P, P]
+    lib.sl_last_error.argtypes = [P]
+    lib.sl_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("sl_free", "sl_state_size", "sl_last_error"):
+            getattr(lib, name).restype = C.c_int
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def velocity(kind, *p):
+    v = SlVelocity()
+    v.kind = int(kind)
+    for i, x in enumerate(p[:6]):
+        v.p[i] = float(x)
+    return v
+
+
+def options(constraints=C_BOUNDARY, rk_order=4, fit=FIT_HARD, bvalue=BV_INTERP, picard_rtol=0.0, picard_cap=0):
+    o = SlOptions()
+    o.constraints, o.rk_order, o.fit, o.bvalue = int(constraints), int(rk_order), int(fit), int(bvalue)
+    o.picard_rtol, o.picard_cap = float(picard_rtol), int(picard_cap)
+    return o
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One mesh on one GPU stream (sl_init ... sl_free)."""
+
+    def __init__(self, dim, kx, ky, box, n, basis=GAUSS_LEGENDRE, precision=FP64, bc=(0, 0, 0, 0),
+                 ghost=0.0, stream=None):
+        import torch
+        self._lib = lib()
+        m = SlMesh()
+        m.dim, m.kx, m.ky = int(dim), int(kx), int(ky)
+        m.x0, m.x1, m.y0, m.y1 = [float(v) for v in box]
+        for i in range(4):
+            m.bc[i] = int(bc[i])
+        m.ghost = float(ghost)
+        m.order = C.POINTER(C.c_int32)()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = self._lib.sl_init(C.byref(m), int(n), int(basis), int(precision),
+                               C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SL_OK:
+            raise SlError(st, self._lib.sl_last_error(None).decode())
+        self._h = h
+        self.dim, self.kx, self.ky, self.n, self.precision = dim, kx, ky, n, precision
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self.size = int(self._lib.sl_state_size(h))
+        self.shape = (kx, n) if dim == 1 else (ky, kx, n, n)
+
+    def _check(self, st):
+        if st != SL_OK:
+            raise SlError(st, self._lib.sl_last_error(self._h).decode())
+
+    def _state(self, t, name):
+        if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.size:
+            raise ValueError(f"{name} must be a contiguous CUDA {self.dtype} tensor of {self.size} values")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sl_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def step(self, phi_in, phi_out, vel, t, dt, opts):
+        self._state(phi_in, "phi_in")
+        self._state(phi_out, "phi_out")
+        self._check(self._lib.sl_step(self._h, _ptr(phi_in), _ptr(phi_out), C.byref(vel), float(t), float(dt),
+                                      C.byref(opts)))
+
+    def run_host(self, host_in, host_out, vel, t0, dt, nsteps, opts):
+        """host_in/host_out: CPU tensors (pinned for speed) of the state dtype."""
+        for t in (host_in, host_out):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.size:
+                raise ValueError("host buffers must be contiguous CPU tensors of the state size and dtype")
+        self._check(self._lib.sl_run_host(self._h, C.c_void_p(host_in.data_ptr()), C.c_void_p(host_out.data_ptr()),
+                                          C.byref(vel), float(t0), float(dt), int(nsteps), C.byref(opts)))
+
+    def mass(self, phi):
+        self._state(phi, "phi")
+        out = C.c_double()
+        self._check(self._lib.sl_mass(self._h, _ptr(phi), C.byref(out)))
+        return out.value
+
+    def energy(self, phi):
+        self._state(phi, "phi")
+        out = C.c_double()
+        self._check(self._lib.sl_energy(self._h, _ptr(phi), C.byref(out)))
+        return out.value
+
+    def sync(self):
+        bits = C.c_uint32()
+        st = self._lib.sl_sync(self._h, C.byref(bits))
+        if st not in (SL_OK, SL_EDEVICE):
+            self._check(st)
+        return bits.value
+
+    def max_dt(self, vel, rule=RULE_HALF_MIN_SPACING):
+        out = C.c_double()
+        self._check(self._lib.sl_max_dt(self._h, C.byref(vel), int(rule), C.byref(out)))
+        return out.value
+
+    def node_coords(self):
+        x = np.empty(self.size)
+        y = np.empty(self.size) if self.dim == 2 else None
+        self._check(self._lib.sl_node_coords(self._h, x.ctypes.data_as(C.c_void_p),
+                                             y.ctypes.data_as(C.c_void_p) if y is not None else None))
+        return (x.reshape(self.shape), y.reshape(self.shape) if y is not None else None)
+
+    def nodes_weights(self, n=None):
+        n = self.n if n is None else n
+        xi, w = np.empty(n), np.empty(n)
+        self._check(self._lib.sl_nodes_weights(self._h, int(n), xi.ctypes.data_as(C.c_void_p),
+                                               w.ctypes.data_as(C.c_void_p)))
+        return xi, w

@@ -1,0 +1,63 @@
+// Global mass and energy (eq. quad summed over elements; the diagnostics of Sec. 5) with a
+// deterministic two-pass reduction in double: a fixed grid of CTAs each sums a fixed strided
+// subset of the elements, then one CTA sums the per-CTA partials in index order.
+#include "sl_internal.h"
+
+namespace sl {
+namespace {
+
+constexpr int RBLOCK = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(RBLOCK) k_partial(int64_t nelem, int nper, int dim, const T* __restrict__ phi,
+                                                   const double* __restrict__ w, int power, double* partial) {
+  __shared__ double red[RBLOCK];
+  __shared__ double ws[NMAX * NMAX];
+  const int nd = dim == 1 ? nper : nper * nper;
+  for (int i = threadIdx.x; i < nd; i += RBLOCK)
+    ws[i] = dim == 1 ? w[i] : w[i / nper] * w[i % nper];
+  __syncthreads();
+  double acc = 0.0;
+  const int64_t total = nelem * nd;
+  for (int64_t idx = (int64_t)blockIdx.x * RBLOCK + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * RBLOCK) {
+    const double v = (double)phi[idx];
+    acc += ws[idx % nd] * (power == 1 ? v : v * v);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = RBLOCK / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(RBLOCK) k_final(int nparts, const double* __restrict__ partial, double scale,
+                                                 double* result) {
+  __shared__ double red[RBLOCK];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += RBLOCK) acc += partial[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = RBLOCK / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *result = red[0] * scale;
+}
+
+}  // namespace
+
+void launch_mass_energy_f64(int64_t nelem, int nper, const double* phi, const double* w, int dim, int power,
+                            double scale, double* partial, double* result, int nblocks, cudaStream_t s) {
+  k_partial<double><<<nblocks, RBLOCK, 0, s>>>(nelem, nper, dim, phi, w, power, partial);
+  k_final<<<1, RBLOCK, 0, s>>>(nblocks, partial, scale, result);
+}
+
+void launch_mass_energy_f32(int64_t nelem, int nper, const float* phi, const double* w, int dim, int power,
+                            double scale, double* partial, double* result, int nblocks, cudaStream_t s) {
+  k_partial<float><<<nblocks, RBLOCK, 0, s>>>(nelem, nper, dim, phi, w, power, partial);
+  k_final<<<1, RBLOCK, 0, s>>>(nblocks, partial, scale, result);
+}
+
+}  // namespace sl

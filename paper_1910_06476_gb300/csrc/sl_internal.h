@@ -1,0 +1,107 @@
+// Internal declarations shared by the host API and the kernels of the GB300 DSEM-SL library.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sl.h"
+
+namespace sl {
+
+constexpr int NMAX = 17;                 // largest node count per direction
+constexpr int MMAX1D = 3;                // linear constraint rows in 1D: left, right, mass
+constexpr double TIE = 1e-13;            // |u.n| at or below this is an upwind tie
+
+// ------------------------------------------------------------------ host tables (tables.cpp)
+
+struct Basis1D {
+  int n = 0;
+  std::vector<double> xi, w, lam;        // nodes on [0,1], weights, barycentric weights
+  std::vector<double> l0, l1;            // Lagrange basis values at xi = 0 and xi = 1
+};
+
+Basis1D make_basis(int n, int basis);
+
+// Dense row-major operators of the constrained fit for one constraint set.
+//   hard: phi_L = phihat + Cpinv (d - C phihat);  q = a - Cpinv (C a)
+//   soft: phi_L = S phihat + SCt d;                q = S a
+struct FitOps {
+  int m = 0, nd = 0;                     // rows, unknowns (n or n^2)
+  std::vector<double> C;                 // m x nd
+  std::vector<double> Cpinv;             // nd x m (hard)
+  std::vector<double> S;                 // nd x nd (soft)
+  std::vector<double> SCt;               // nd x m (soft)
+};
+
+// 1D constraint rows for a mask (left face, right face, mass in the reference measure).
+FitOps make_fit_1d(const Basis1D& b, unsigned mask);
+// 2D constraint rows: W, E, S, N faces (n each, at the tangential nodes), then mass.
+FitOps make_fit_2d(const Basis1D& b, unsigned mask, bool soft);
+void finish_fit(FitOps& f, bool soft);
+
+// ------------------------------------------------------------------ device-side parameter blocks
+
+struct Tables1D {                         // device pointers into one table buffer
+  const double* xi;
+  const double* w;
+  const double* lam;
+  const double* l0;
+  const double* l1;
+  const double* Cpinv;                   // [n][m] for the active row set
+  const double* S;                       // [n][n]
+  const double* SCt;                     // [n][m]
+};
+
+struct StepParams {
+  int K;                                 // elements (1D)
+  int kx, ky;
+  double x0, hx, y0, hy;
+  int bc[4];
+  double ghost;
+  int vel_kind;
+  double vp[6];
+  double t, dt;
+  int rk;
+  unsigned cons;
+  int fit;
+  int bvalue;
+  int m;                                 // active linear rows
+  double picard_rtol;
+  int picard_cap;
+};
+
+void launch_step1d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in,
+                       double* out, unsigned* status, cudaStream_t s);
+void launch_mass_energy_f64(int64_t nelem, int nper, const double* phi, const double* w, int dim,
+                            int power, double scale, double* partial, double* result, int nblocks,
+                            cudaStream_t s);
+void launch_mass_energy_f32(int64_t nelem, int nper, const float* phi, const double* w, int dim,
+                            int power, double scale, double* partial, double* result, int nblocks,
+                            cudaStream_t s);
+
+}  // namespace sl
+
+// ------------------------------------------------------------------ context
+
+struct sl_ctx {
+  sl_mesh mesh{};
+  std::vector<int32_t> orders;
+  int n = 0, basis = 0, precision = 0;
+  cudaStream_t stream = nullptr;
+  int64_t nvals = 0;
+  sl::Basis1D b;
+  // fit operators per constraint mask (index = mask & 3 for linear rows) and fit mode
+  sl::FitOps fit[4][2];
+  double* d_tables = nullptr;            // device table buffer
+  size_t table_off[4][2][3] = {};        // offsets of Cpinv, S, SCt per mask/mode
+  size_t off_xi = 0, off_w = 0, off_lam = 0, off_l0 = 0, off_l1 = 0;
+  unsigned* d_status = nullptr;
+  double* d_partial = nullptr;           // reduction workspace
+  double* d_result = nullptr;
+  int red_blocks = 0;
+  void* d_io = nullptr;                  // device state pair for sl_run_host
+  std::string err;
+};
