@@ -35,6 +35,10 @@ in the design notes):
       hard fit we keep its fixed point and reach it by taking the Picard correction
       direction from the previous iterate and solving the energy equation exactly along it
       (a scalar quadratic, smallest root).  The soft fit iterates the paper's system as is.
+      The energy row is applied only when the linear fit misses the energy target by more
+      than 1e-12 relative: on nearly constant data the row is almost a multiple of the mass
+      row, its direction is set by a variation near rounding level, and a correction would
+      only amplify rounding noise.
   R8  Upwinding by the sign of u.n at the face point (at t^{n+1} for boundary values, at the
       stage time for fluxes); |u.n| <= TIE is a tie: interior faces average both traces,
       non-periodic domain faces keep their own trace.
@@ -69,6 +73,7 @@ TIE = 1e-13                 # |u.n| at or below this is a tie (R8)
 RANK_RTOL = 1e-12           # rank decision of the pivoted QR (R6)
 PICARD_RTOL = 1e-13         # default energy-iteration tolerance, relative to max|phihat| (R7)
 PICARD_CAP = 60
+ENERGY_SKIP_RTOL = 1e-12    # energy row applied only when the linear fit misses it by more (R7)
 
 # ============================================================================ L0 tables
 
@@ -352,7 +357,10 @@ def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode
         if energy_row_weights is None:
             return phiL, 0, True
         W = energy_row_weights
-        gamma = float(np.dot(W, phiL * phiL)) - E_target
+        EL = float(np.dot(W, phiL * phiL))
+        gamma = EL - E_target
+        if abs(gamma) <= ENERGY_SKIP_RTOL * max(abs(E_target), EL):
+            return phiL, 0, True
         phi = phiL
         feasible = True
         for it in range(1, cap + 1):
@@ -369,6 +377,9 @@ def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode
         return phi, cap, False
     phi = fit_soft(phihat, C_lin, d_lin)
     if energy_row_weights is None:
+        return phi, 0, True
+    EL = float(np.dot(energy_row_weights, phi * phi))
+    if abs(EL - E_target) <= ENERGY_SKIP_RTOL * max(abs(E_target), EL):
         return phi, 0, True
     for it in range(1, cap + 1):
         a = energy_row_weights * phi

@@ -314,8 +314,10 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
 #pragma unroll
     for (int i = 0; i < NN; ++i) EL += sm.w[i] * phL[i] * phL[i];
     const double gamma = EL - Et;
-    bool conv = false, feasible = true;
-    for (int it = 0; it < P.picard_cap; ++it) {
+    // energy row only when the linear fit misses its target beyond rounding level
+    const bool apply = fabs(gamma) > ENERGY_SKIP_RTOL * fmax(fabs(Et), EL);
+    bool conv = !apply, feasible = true;
+    for (int it = 0; apply && it < P.picard_cap; ++it) {
       double a[NN], qv[NN];
 #pragma unroll
       for (int i = 0; i < NN; ++i) a[i] = sm.w[i] * res_phi[i];
