@@ -20,7 +20,10 @@
  *     layout: 1D [K][n]; 2D [ky][kx][n][n] with the x index fastest (node (i, j) of element
  *     (ex, ey) at offset ((ey*kx + ex)*n + j)*n + i); p-adaptive 2D meshes store element e
  *     (row-major over (ey, ex)) at offset off[e] with n_e*n_e values, off being the exclusive
- *     prefix sum of n_e^2.  Element type: double for SL_FP64, float for SL_MIXED.
+ *     prefix sum of n_e^2.  SL_FP64 state is one double per node.  SL_MIXED state is
+ *     double-float: a plane of sl_state_size floats "hi" followed by a plane of as many floats
+ *     "lo", the node value being hi + lo (about 48 significant bits); sl_pack and sl_unpack
+ *     convert from and to doubles.  Either way a state buffer has sl_state_bytes bytes.
  *   - Pointers documented as "host" are host memory; everything else is device memory.
  *   - The library owns its tables, operators and workspace (allocated in sl_init and freed in
  *     sl_free).  All device work is enqueued on the stream given to sl_init; no call
@@ -59,8 +62,10 @@ typedef enum {
 enum { SL_GAUSS_LEGENDRE = 0, SL_CHEB_GAUSS = 1 };
 
 /* Arithmetic: SL_FP64 computes every step in double precision on double state.
- * SL_MIXED keeps float state and float bulk arithmetic, with the constraint integrals and
- * the scalars of the energy iteration carried to double-precision accuracy. */
+ * SL_MIXED keeps double-float state and does the bulk arithmetic in float on increments
+ * relative to a per-element reference value (so float rounding scales with the variation
+ * inside an element), writing results back exactly.  In 1D it requires a constant velocity:
+ * the whole linear step is then one operator shared by all elements. */
 enum { SL_FP64 = 0, SL_MIXED = 1 };
 
 /* Domain faces: periodic wrap, or an inflow face that sees the constant ghost value
@@ -134,16 +139,24 @@ sl_status sl_init(const sl_mesh* mesh, int n, int basis, int precision, void* cu
 void sl_free(sl_ctx* ctx);
 
 /* Advance the state by one step from time t to t + dt (Sec. 4, steps a-d).  phi_in and
- * phi_out are distinct device buffers of sl_state_size values of the context's element
- * type; phi_in is only read.  Returns SL_ECFL when |u|max dt exceeds the element width. */
+ * phi_out are distinct device buffers of sl_state_bytes bytes in the context's state format;
+ * phi_in is only read.  Returns SL_ECFL when |u|max dt exceeds the element width, and
+ * SL_EUNSUPPORTED for a combination this build does not implement (nothing is enqueued). */
 sl_status sl_step(sl_ctx* ctx, const void* phi_in, void* phi_out, const sl_velocity* vel,
                   double t, double dt, const sl_options* opt);
 
-/* Advance nsteps steps from t0 with a fixed dt, starting from and ending in HOST buffers:
- * copies host_in to the device, steps, copies the result to host_out, then synchronises.
- * host_in and host_out hold sl_state_size values of the element type and may alias. */
-sl_status sl_run_host(sl_ctx* ctx, const void* host_in, void* host_out, const sl_velocity* vel,
+/* Advance nsteps steps from t0 with a fixed dt, starting from and ending in HOST buffers of
+ * sl_state_size doubles (node values in state layout, whatever the precision): copies host_in
+ * to the device (converting to the state format), steps, converts back and copies the result
+ * to host_out, then synchronises.  host_in and host_out may alias.  The device buffers this
+ * needs are allocated on the first call and kept until sl_free. */
+sl_status sl_run_host(sl_ctx* ctx, const double* host_in, double* host_out, const sl_velocity* vel,
                       double t0, double dt, int nsteps, const sl_options* opt);
+
+/* Convert sl_state_size doubles (device) into the context's state format (device, sl_state_bytes
+ * bytes), and back.  For SL_FP64 these are plain copies.  Enqueued on the context's stream. */
+sl_status sl_pack(sl_ctx* ctx, const double* src, void* dst);
+sl_status sl_unpack(sl_ctx* ctx, const void* src, double* dst);
 
 /* Global mass sum_k integral phi and energy sum_k integral phi^2 (eq. quad summed over the
  * elements, diagnostics of Sec. 5), accumulated in double in a fixed order (deterministic).
@@ -157,8 +170,9 @@ sl_status sl_sync(sl_ctx* ctx, uint32_t* status_bits);
 /* Largest dt allowed by a time-step rule for this mesh and velocity (host computation). */
 sl_status sl_max_dt(const sl_ctx* ctx, const sl_velocity* vel, int rule, double* dt);
 
-/* Number of node values of the state. */
+/* Number of node values of the state, and bytes of one state buffer (-1 for a null ctx). */
 int64_t sl_state_size(const sl_ctx* ctx);
+int64_t sl_state_bytes(const sl_ctx* ctx);
 
 /* Physical node coordinates in state layout, written to host arrays of sl_state_size
  * doubles (y may be null in 1D), for setting up initial data. */

@@ -24,8 +24,9 @@ BV_INTERP, BV_BACKTRACK = 0, 1
 RULE_HALF_MIN_SPACING, RULE_PAPER = 0, 1
 ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV = 1, 2, 4
 
-EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run_host", "sl_mass", "sl_energy", "sl_sync",
-           "sl_max_dt", "sl_state_size", "sl_node_coords", "sl_nodes_weights", "sl_last_error"]
+EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
+           "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",
+           "sl_last_error"]
 
 
 class SlMesh(C.Structure):
@@ -62,6 +63,10 @@ def load_library(path=LIB_PATH):
     lib.sl_step.argtypes = [P, P, P, C.POINTER(SlVelocity), C.c_double, C.c_double, C.POINTER(SlOptions)]
     lib.sl_run_host.argtypes = [P, P, P, C.POINTER(SlVelocity), C.c_double, C.c_double, C.c_int,
                                 C.POINTER(SlOptions)]
+    lib.sl_pack.argtypes = [P, P, P]
+    lib.sl_unpack.argtypes = [P, P, P]
+    lib.sl_state_bytes.argtypes = [P]
+    lib.sl_state_bytes.restype = C.c_int64
     lib.sl_mass.argtypes = [P, P, C.POINTER(C.c_double)]
     lib.sl_energy.argtypes = [P, P, C.POINTER(C.c_double)]
     lib.sl_sync.argtypes = [P, C.POINTER(C.c_uint32)]
@@ -73,7 +78,7 @@ def load_library(path=LIB_PATH):
     lib.sl_last_error.argtypes = [P]
     lib.sl_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("sl_free", "sl_state_size", "sl_last_error"):
+        if name not in ("sl_free", "sl_state_size", "sl_state_bytes", "sl_last_error"):
             getattr(lib, name).restype = C.c_int
     return lib
 
@@ -132,14 +137,37 @@ class Context:
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.size = int(self._lib.sl_state_size(h))
         self.shape = (kx, n) if dim == 1 else (ky, kx, n, n)
+        # number of state elements of self.dtype in one state buffer (two float planes when mixed)
+        self.numel = self.size if precision == FP64 else 2 * self.size
 
     def _check(self, st):
         if st != SL_OK:
             raise SlError(st, self._lib.sl_last_error(self._h).decode())
 
     def _state(self, t, name):
-        if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.size:
-            raise ValueError(f"{name} must be a contiguous CUDA {self.dtype} tensor of {self.size} values")
+        if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.numel:
+            raise ValueError(f"{name} must be a contiguous CUDA {self.dtype} tensor of {self.numel} values")
+
+    def new_state(self):
+        import torch
+        return torch.empty(self.numel, dtype=self.dtype, device="cuda")
+
+    def pack(self, phi64):
+        """Device doubles (state layout) -> a new state buffer in this context's format."""
+        import torch
+        if not phi64.is_cuda or phi64.dtype != torch.float64 or not phi64.is_contiguous() or phi64.numel() != self.size:
+            raise ValueError("pack expects a contiguous CUDA float64 tensor of the state size")
+        out = self.new_state()
+        self._check(self._lib.sl_pack(self._h, _ptr(phi64), _ptr(out)))
+        return out
+
+    def unpack(self, state):
+        """A state buffer -> a new CUDA float64 tensor of node values (state layout)."""
+        import torch
+        self._state(state, "state")
+        out = torch.empty(self.size, dtype=torch.float64, device="cuda")
+        self._check(self._lib.sl_unpack(self._h, _ptr(state), _ptr(out)))
+        return out
 
     def close(self):
         if getattr(self, "_h", None):
@@ -155,10 +183,11 @@ class Context:
                                       C.byref(opts)))
 
     def run_host(self, host_in, host_out, vel, t0, dt, nsteps, opts):
-        """host_in/host_out: CPU tensors (pinned for speed) of the state dtype."""
+        """host_in/host_out: CPU float64 tensors (pinned for speed) of node values."""
+        import torch
         for t in (host_in, host_out):
-            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != self.size:
-                raise ValueError("host buffers must be contiguous CPU tensors of the state size and dtype")
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != self.size:
+                raise ValueError("host buffers must be contiguous CPU float64 tensors of the state size")
         self._check(self._lib.sl_run_host(self._h, C.c_void_p(host_in.data_ptr()), C.c_void_p(host_out.data_ptr()),
                                           C.byref(vel), float(t0), float(dt), int(nsteps), C.byref(opts)))
 

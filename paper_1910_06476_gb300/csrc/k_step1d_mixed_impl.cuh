@@ -1,0 +1,198 @@
+#pragma once
+// 1D DSEM-SL step, mixed precision, shared operator (uniform mesh, constant velocity).
+//
+// State: double-float, a hi plane and a lo plane of floats (phi = hi + lo, about 48 bits).
+// Every element of a CTA tile is advanced by one thread:
+//   - its values and its upwind neighbour's are read relative to a per-element reference
+//     ref = hi of its first node: psi = (hi - ref) + lo, in float.  The step operator
+//     reproduces constants, so phi^{n+1} = ref + G psi and the float rounding scales with the
+//     variation inside the stencil rather than with |phi|;
+//   - the linear step (remap eq. 4.9, upwinded boundary values eq. 4.12a, mass target
+//     eq. remap_mass, constrained fit eq. matrix_a) is one shared operator applied in float;
+//   - the energy constraint (eq. remap_energy) is solved per element; its mismatch is formed
+//     from increments only, so that the decision to apply it is free of float cancellation;
+//   - the result is written back exactly as ref + psi by TwoSum (Knuth), hi = fl(ref + psi),
+//     lo = (ref + psi) - hi.
+// The tile (and its upwind halo element) is staged through shared memory with coalesced loads
+// and stores; the kernel reads 8 and writes 8 bytes per node from HBM.
+#include "sl_internal.h"
+
+namespace sl {
+namespace k1m {
+
+constexpr int TILE = 256;                  // elements (threads) per CTA
+
+__device__ __forceinline__ int wrap_elem(int e, int K, bool periodic) {
+  if (e >= 0 && e < K) return e;
+  if (!periodic) return -1;
+  e %= K;
+  return e < 0 ? e + K : e;
+}
+
+template <int NN>
+__global__ void __launch_bounds__(TILE) k_step1d_mixed(const __grid_constant__ Mixed1DParams P,
+                                                       const float* __restrict__ in, float* __restrict__ out,
+                                                       unsigned* status) {
+  __shared__ float shi[(TILE + 1) * NN];
+  __shared__ float slo[(TILE + 1) * NN];
+  const int tid = threadIdx.x;
+  const int K = P.K;
+  const int64_t plane = (int64_t)K * NN;
+  const int e0 = blockIdx.x * TILE;
+  // tile rows: left upwind -> [e0-1, e0+TILE), right upwind -> [e0, e0+TILE]
+  const int first = P.left_up ? e0 - 1 : e0;
+  for (int idx = tid; idx < (TILE + 1) * NN; idx += TILE) {
+    const int row = idx / NN, i = idx - row * NN;
+    const int e = wrap_elem(first + row, K, P.periodic != 0);
+    float h = 0.0f, l = 0.0f;
+    if (e >= 0) {
+      h = in[(int64_t)e * NN + i];
+      l = in[plane + (int64_t)e * NN + i];
+    }
+    shi[idx] = h;
+    slo[idx] = l;
+  }
+  __syncthreads();
+
+  const int e = e0 + tid;
+  const bool active = e < K;
+  const int own = P.left_up ? tid + 1 : tid;
+  const int up = P.left_up ? tid : tid + 1;
+  const int eup = wrap_elem(P.left_up ? e - 1 : e + 1, K, P.periodic != 0);
+  float res[NN];
+  float ref = 0.0f;
+  bool ok = true;
+  if (active) {
+    ref = shi[own * NN];
+    float ps[NN], pu[NN];
+#pragma unroll
+    for (int i = 0; i < NN; ++i) ps[i] = (shi[own * NN + i] - ref) + slo[own * NN + i];
+    if (eup >= 0) {
+#pragma unroll
+      for (int i = 0; i < NN; ++i) pu[i] = (shi[up * NN + i] - ref) + slo[up * NN + i];
+    } else {
+      const float g = (float)(P.ghost - (double)ref);   // ghost value at the inflow domain face
+#pragma unroll
+      for (int i = 0; i < NN; ++i) pu[i] = g;
+    }
+    // shared linear operator
+    float pl[NN];
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NN; ++i) acc = fmaf(P.Gs[j * NN + i], ps[i], acc);
+#pragma unroll
+      for (int i = 0; i < NN; ++i) acc = fmaf(P.Gu[j * NN + i], pu[i], acc);
+      pl[j] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < NN; ++j) res[j] = pl[j];
+
+    if (P.energy_on) {
+      // energy mismatch from increments: variance part, plus 2 ref x mass residual when the mass
+      // row is not enforced (with it, that bracket vanishes identically)
+      float gv = 0.0f, gm = 0.0f, escale = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NN; ++i) {
+        gv = fmaf(P.w[i], pl[i] * pl[i] - ps[i] * ps[i], gv);
+        gm = fmaf(P.w[i], pl[i] - ps[i], gm);
+        const float phv = ref + ps[i];
+        escale = fmaf(P.w[i], phv * phv, escale);
+      }
+      for (int s = 0; s < P.nst; ++s) {
+        float es = 0.0f, eu = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NN; ++i) { es = fmaf(P.E[s][i], ps[i], es); eu = fmaf(P.E[s][i], pu[i], eu); }
+        gv = fmaf(P.lam * P.fb[s], es * es - eu * eu, gv);
+        gm = fmaf(P.lam * P.fb[s], es - eu, gm);
+      }
+      const float gamma = P.mass_on ? gv : fmaf(2.0f * ref, gm, gv);
+      if (fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {
+        float pmax = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NN; ++i) pmax = fmaxf(pmax, fabsf(pl[i]));
+        const float tol = fmaxf(P.picard_rtol * fabsf(ref), 2.4e-7f * pmax) + 1e-37f;
+        bool conv = false, feasible = true;
+        for (int it = 0; it < P.picard_cap; ++it) {
+          float av[NN], q[NN];
+#pragma unroll
+          for (int i = 0; i < NN; ++i) av[i] = P.w[i] * (P.mass_on ? res[i] : ref + res[i]);
+          float ca[MMAX1D];
+          for (int k = 0; k < P.m; ++k) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NN; ++i) acc = fmaf(P.C[k * NN + i], av[i], acc);
+            ca[k] = acc;
+          }
+#pragma unroll
+          for (int j = 0; j < NN; ++j) {
+            float acc = av[j];
+            for (int k = 0; k < P.m; ++k) acc = fmaf(-P.Cp[j * P.m + k], ca[k], acc);
+            q[j] = acc;
+          }
+          float alpha = 0.0f, beta = 0.0f, wq = 0.0f;
+#pragma unroll
+          for (int i = 0; i < NN; ++i) {
+            alpha = fmaf(P.w[i] * pl[i], q[i], alpha);
+            beta = fmaf(P.w[i] * q[i], q[i], beta);
+            wq = fmaf(P.w[i], q[i], wq);
+          }
+          if (!P.mass_on) alpha = fmaf(ref, wq, alpha);
+          float s;
+          if (beta <= 0.0f) { s = 0.0f; feasible = gamma <= 0.0f; }
+          else {
+            const float disc = alpha * alpha - beta * gamma;
+            if (disc < 0.0f) { s = -alpha / beta; feasible = false; }
+            else {
+              const float root = sqrtf(disc);
+              const float den = alpha + (alpha >= 0.0f ? root : -root);
+              s = den == 0.0f ? 0.0f : -gamma / den;
+              feasible = true;
+            }
+          }
+          float delta = 0.0f;
+#pragma unroll
+          for (int i = 0; i < NN; ++i) {
+            const float nv = fmaf(s, q[i], pl[i]);
+            delta = fmaxf(delta, fabsf(nv - res[i]));
+            res[i] = nv;
+          }
+          if (delta <= tol) { conv = feasible; break; }
+        }
+        ok = conv;
+      }
+    }
+  }
+  __syncthreads();                          // tile rows are rewritten below
+  bool finite = true;
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+      // TwoSum: hi + lo == ref + res exactly
+      const float s = ref + res[j];
+      const float bb = s - ref;
+      const float err = (ref - (s - bb)) + (res[j] - bb);
+      shi[tid * NN + j] = s;
+      slo[tid * NN + j] = err;
+      finite = finite && isfinite(s);
+    }
+  }
+  __syncthreads();
+  const int nact = min(TILE, K - e0);
+  for (int idx = tid; idx < nact * NN; idx += TILE) {
+    out[(int64_t)e0 * NN + idx] = shi[idx];
+    out[plane + (int64_t)e0 * NN + idx] = slo[idx];
+  }
+  const unsigned bits = (finite ? 0u : SL_ST_NONFINITE) | (ok ? 0u : SL_ST_PICARD_NOCONV);
+  if (bits) atomicOr(status, bits);
+}
+
+template <int NN>
+void launch_n(const Mixed1DParams& p, const float* in, float* out, unsigned* st, cudaStream_t s) {
+  const int grid = (p.K + TILE - 1) / TILE;
+  k_step1d_mixed<NN><<<grid, TILE, 0, s>>>(p, in, out, st);
+}
+
+}  // namespace k1m
+}  // namespace sl

@@ -26,7 +26,8 @@ sl_status fail(sl_ctx* c, sl_status st, const std::string& msg) {
     if (e_ != cudaSuccess) return fail(ctx, SL_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-size_t elt_bytes(const sl_ctx* c) { return c->precision == SL_FP64 ? sizeof(double) : sizeof(float); }
+// bytes of state per node: one double (SL_FP64) or a hi and a lo float (SL_MIXED)
+size_t node_bytes(const sl_ctx*) { return 8; }
 
 void max_speed(const sl_ctx* c, const sl_velocity* v, double& um, double& vm) {
   const sl_mesh& M = c->mesh;
@@ -154,6 +155,7 @@ void sl_free(sl_ctx* c) {
   cudaFree(c->d_partial);
   cudaFree(c->d_result);
   cudaFree(c->d_io);
+  cudaFree(c->d_io64);
   delete c;
 }
 
@@ -205,6 +207,27 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
     Tables1D tb{T + c->off_xi, T + c->off_w, T + c->off_lam, T + c->off_l0, T + c->off_l1,
                 T + off[0], T + off[1], T + off[2]};
     launch_step1d_f64(c->n, P, tb, (const double*)phi_in, (double*)phi_out, c->d_status, c->stream);
+  } else if (M.dim == 1 && c->precision == SL_MIXED) {
+    if (vel->kind != SL_VEL_CONST)
+      return fail(c, SL_EUNSUPPORTED, "the 1D mixed path needs a constant velocity (shared operator)");
+    if (opt->bvalue != SL_BV_INTERP)
+      return fail(c, SL_EUNSUPPORTED, "the 1D mixed path uses interpolated interface values");
+    if (!c->mix_valid || c->mix_a != vel->p[0] || c->mix_dt != dt || c->mix_cons != opt->constraints ||
+        c->mix_rk != opt->rk_order || c->mix_fit != opt->fit) {
+      std::string why;
+      if (!build_mixed1d(c, c->fit[lin][opt->fit == SL_FIT_SOFT], vel->p[0], dt, opt->constraints, opt->rk_order,
+                         opt->fit, c->mix, why))
+        return fail(c, SL_EUNSUPPORTED, why);
+      c->mix_valid = true;
+      c->mix_a = vel->p[0];
+      c->mix_dt = dt;
+      c->mix_cons = opt->constraints;
+      c->mix_rk = opt->rk_order;
+      c->mix_fit = opt->fit;
+    }
+    c->mix.picard_rtol = (float)P.picard_rtol;
+    c->mix.picard_cap = P.picard_cap;
+    launch_step1d_mixed(c->mix, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream);
   } else {
     return fail(c, SL_EUNSUPPORTED, "this dimension/precision combination is not built yet");
   }
@@ -212,28 +235,69 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
   return SL_OK;
 }
 
-sl_status sl_run_host(sl_ctx* c, const void* host_in, void* host_out, const sl_velocity* vel, double t0, double dt,
-                      int nsteps, const sl_options* opt) {
+sl_status sl_run_host(sl_ctx* c, const double* host_in, double* host_out, const sl_velocity* vel, double t0,
+                      double dt, int nsteps, const sl_options* opt) {
   if (!c) return SL_EINVAL;
   if (!host_in || !host_out || nsteps < 0) return fail(c, SL_EINVAL, "bad host buffers or step count");
-  const size_t bytes = (size_t)c->nvals * elt_bytes(c);
+  const size_t bytes = (size_t)c->nvals * node_bytes(c);
   if (!c->d_io) {
     if (cudaMalloc(&c->d_io, 2 * bytes) != cudaSuccess) {
       cudaGetLastError();
       c->d_io = nullptr;
       return fail(c, SL_ENOMEM, "device allocation of the run buffers failed");
     }
+    if (c->precision == SL_MIXED && cudaMalloc(&c->d_io64, (size_t)c->nvals * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(c->d_io);
+      c->d_io = nullptr;
+      c->d_io64 = nullptr;
+      return fail(c, SL_ENOMEM, "device allocation of the run buffers failed");
+    }
   }
   char* a = (char*)c->d_io;
   char* b = a + bytes;
-  SL_CUDA(c, cudaMemcpyAsync(a, host_in, bytes, cudaMemcpyHostToDevice, c->stream));
+  if (c->precision == SL_FP64) {
+    SL_CUDA(c, cudaMemcpyAsync(a, host_in, bytes, cudaMemcpyHostToDevice, c->stream));
+  } else {
+    SL_CUDA(c, cudaMemcpyAsync(c->d_io64, host_in, (size_t)c->nvals * sizeof(double), cudaMemcpyHostToDevice,
+                               c->stream));
+    launch_pack(c->nvals, c->d_io64, (float*)a, c->stream);
+  }
   for (int s = 0; s < nsteps; ++s) {
     sl_status st = sl_step(c, a, b, vel, t0 + s * dt, dt, opt);
     if (st != SL_OK) return st;
     std::swap(a, b);
   }
-  SL_CUDA(c, cudaMemcpyAsync(host_out, a, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (c->precision == SL_FP64) {
+    SL_CUDA(c, cudaMemcpyAsync(host_out, a, bytes, cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    launch_unpack(c->nvals, (const float*)a, c->d_io64, c->stream);
+    SL_CUDA(c, cudaMemcpyAsync(host_out, c->d_io64, (size_t)c->nvals * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+  }
   SL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SL_OK;
+}
+
+sl_status sl_pack(sl_ctx* c, const double* src, void* dst) {
+  if (!c) return SL_EINVAL;
+  if (!src || !dst) return fail(c, SL_EINVAL, "null argument");
+  if (c->precision == SL_FP64)
+    SL_CUDA(c, cudaMemcpyAsync(dst, src, (size_t)c->nvals * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  else
+    launch_pack(c->nvals, src, (float*)dst, c->stream);
+  SL_CUDA(c, cudaGetLastError());
+  return SL_OK;
+}
+
+sl_status sl_unpack(sl_ctx* c, const void* src, double* dst) {
+  if (!c) return SL_EINVAL;
+  if (!src || !dst) return fail(c, SL_EINVAL, "null argument");
+  if (c->precision == SL_FP64)
+    SL_CUDA(c, cudaMemcpyAsync(dst, src, (size_t)c->nvals * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  else
+    launch_unpack(c->nvals, (const float*)src, dst, c->stream);
+  SL_CUDA(c, cudaGetLastError());
   return SL_OK;
 }
 
@@ -247,8 +311,8 @@ static sl_status integral(sl_ctx* c, const void* phi, double* total, int power) 
     launch_mass_energy_f64(nel, c->n, (const double*)phi, c->d_tables + c->off_w, M.dim, power, hx * hy,
                            c->d_partial, c->d_result, c->red_blocks, c->stream);
   else
-    launch_mass_energy_f32(nel, c->n, (const float*)phi, c->d_tables + c->off_w, M.dim, power, hx * hy,
-                           c->d_partial, c->d_result, c->red_blocks, c->stream);
+    launch_mass_energy_pair(nel, c->n, (const float*)phi, c->d_tables + c->off_w, M.dim, power, hx * hy,
+                            c->d_partial, c->d_result, c->red_blocks, c->stream);
   SL_CUDA(c, cudaGetLastError());
   SL_CUDA(c, cudaMemcpyAsync(total, c->d_result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   SL_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -292,6 +356,8 @@ sl_status sl_max_dt(const sl_ctx* c, const sl_velocity* vel, int rule, double* d
 }
 
 int64_t sl_state_size(const sl_ctx* c) { return c ? c->nvals : -1; }
+
+int64_t sl_state_bytes(const sl_ctx* c) { return c ? c->nvals * (int64_t)node_bytes(c) : -1; }
 
 sl_status sl_node_coords(const sl_ctx* c, double* x, double* y) {
   if (!c || !x || (c->mesh.dim == 2 && !y)) return SL_EINVAL;

@@ -9,6 +9,8 @@
 
 #include "../../include/sl.h"
 
+struct sl_ctx;
+
 namespace sl {
 
 constexpr int NMAX = 17;                 // largest node count per direction
@@ -76,12 +78,33 @@ struct StepParams {
 
 void launch_step1d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in,
                        double* out, unsigned* status, cudaStream_t s);
+
+// Kernel parameter block of the 1D shared-operator (mixed precision) step; passed by value.
+struct Mixed1DParams {
+  int n, K, left_up, periodic, m, mass_on, energy_on, nst;
+  double ghost;
+  float lam;                             // |a| dt / h
+  float picard_rtol;
+  int picard_cap;
+  float Gs[NMAX * NMAX], Gu[NMAX * NMAX];  // [j][i]
+  float w[NMAX];
+  float fb[3];                           // merged RK weights of the distinct stage times
+  float E[3][NMAX];                      // basis at the characteristic feet of the outflow face
+  float C[MMAX1D * NMAX];                // linear constraint rows
+  float Cp[NMAX * MMAX1D];               // their pseudo-inverse (hard fit)
+};
+
+bool build_mixed1d(const sl_ctx* c, const FitOps& fit, double a, double dt, unsigned cons, int rk, int fitmode,
+                   Mixed1DParams& P, std::string& err);
+void launch_step1d_mixed(const Mixed1DParams& p, const float* in, float* out, unsigned* status, cudaStream_t s);
+void launch_pack(int64_t nvals, const double* src, float* dst, cudaStream_t s);
+void launch_unpack(int64_t nvals, const float* src, double* dst, cudaStream_t s);
 void launch_mass_energy_f64(int64_t nelem, int nper, const double* phi, const double* w, int dim,
                             int power, double scale, double* partial, double* result, int nblocks,
                             cudaStream_t s);
-void launch_mass_energy_f32(int64_t nelem, int nper, const float* phi, const double* w, int dim,
-                            int power, double scale, double* partial, double* result, int nblocks,
-                            cudaStream_t s);
+void launch_mass_energy_pair(int64_t nelem, int nper, const float* phi, const double* w, int dim,
+                             int power, double scale, double* partial, double* result, int nblocks,
+                             cudaStream_t s);
 
 }  // namespace sl
 
@@ -103,6 +126,13 @@ struct sl_ctx {
   double* d_partial = nullptr;           // reduction workspace
   double* d_result = nullptr;
   int red_blocks = 0;
-  void* d_io = nullptr;                  // device state pair for sl_run_host
+  void* d_io = nullptr;                  // device buffers for sl_run_host
+  double* d_io64 = nullptr;
+  // cached shared operator of the mixed 1D path, keyed on (a, dt, constraints, rk, fit)
+  bool mix_valid = false;
+  double mix_a = 0, mix_dt = 0;
+  unsigned mix_cons = 0;
+  int mix_rk = 0, mix_fit = 0;
+  sl::Mixed1DParams mix{};
   std::string err;
 };

@@ -213,7 +213,7 @@ def test_run_host_matches_device_steps(sl):
     dt = ctx.max_dt(gv)
     phi = sl_inputs.random_state((200, 9), 2)
     opts = sl.options(3, 4)
-    host_in = torch.tensor(phi).pin_memory()
+    host_in = torch.tensor(phi.ravel()).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     ctx.run_host(host_in, host_out, gv, 0.0, dt, 3, opts)
     a = torch.tensor(phi, device="cuda")
@@ -221,4 +221,4 @@ def test_run_host_matches_device_steps(sl):
     for s in range(3):
         ctx.step(a, b, gv, s * dt, dt, opts)
         a, b = b, a
-    assert torch.equal(a.cpu(), host_out)
+    assert torch.equal(a.cpu().ravel(), host_out)

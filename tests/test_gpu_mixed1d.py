@@ -1,0 +1,164 @@
+"""GPU parity of the mixed-precision 1D shared-operator path (double-float state, float bulk
+arithmetic on per-element increments) against the FP64 oracle and the FP64 GPU path.
+
+Bound: relative L2 <= 1e-6 against FP64 after 1 and after 1000 steps."""
+import numpy as np
+import pytest
+
+import sl_inputs
+from oracle import sl_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def sl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_06476_gb300 import build as B
+    B.build()
+    import paper_1910_06476_gb300 as pkg
+    return pkg
+
+
+def mixed_ctx(sl, K, n, bc=0, ghost=0.0, basis=0):
+    return sl.Context(1, K, 1, (0.0, 1.0, 0, 0), n, basis, sl.MIXED, (bc,) * 4, ghost)
+
+
+def test_pack_unpack_roundtrip(sl):
+    ctx = mixed_ctx(sl, 100, 7)
+    phi = torch.tensor(sl_inputs.random_state((100, 7), 0) * 1e3, device="cuda")
+    back = ctx.unpack(ctx.pack(phi))
+    rel = (back - phi).abs().max().item() / phi.abs().max().item()
+    assert rel < 1e-14
+
+
+CASES = [
+    # K, n, a, cons, rk, fit, bc
+    (300, 9, 1.0, 1, 4, 0, 0),
+    (300, 9, 1.0, 3, 4, 0, 0),
+    (300, 9, 1.0, 7, 4, 0, 0),
+    (300, 5, -0.7, 7, 2, 0, 0),
+    (257, 13, 1.0, 7, 3, 0, 0),
+    (130, 17, 0.5, 7, 4, 0, 0),
+    (130, 2, 1.0, 3, 4, 0, 0),
+    (64, 7, 1.0, 3, 1, 1, 0),
+    (64, 6, 0.9, 7, 4, 0, 1),
+    (64, 6, -0.9, 3, 4, 0, 1),
+    (1, 6, 1.0, 3, 4, 0, 0),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"K{c[0]}n{c[1]}a{c[2]}c{c[3]}rk{c[4]}f{c[5]}bc{c[6]}" for c in CASES])
+def test_mixed_step_parity(sl, case):
+    K, n, a, cons, rk, fit, bc = case
+    ctx = mixed_ctx(sl, K, n, bc, 0.25)
+    setup = O.Setup(1, K, 1, (0.0, 1.0, 0, 0), n, 0, (bc,) * 4, 0.25)
+    gv = sl.velocity(sl.VEL_CONST, a)
+    dt = ctx.max_dt(gv)
+    x, _ = ctx.node_coords()
+    phi = 1.0 + 0.5 * np.sin(2 * np.pi * x) + 0.05 * sl_inputs.random_state(x.shape, K + n)
+    st = ctx.pack(torch.tensor(phi.ravel(), device="cuda"))
+    out = ctx.new_state()
+    ctx.step(st, out, gv, 0.1, dt, sl.options(cons, rk, fit))
+    bits = ctx.sync()
+    got = ctx.unpack(out).cpu().numpy().reshape(K, n)
+    ref, infos = O.step_1d(setup, phi, O.StepOpts(O.Vel(O.VEL_CONST, (a, 0, 0, 0, 0, 0)), 0.1, dt, cons, rk, fit))
+    conv = np.array([infos[k]["converged"] for k in range(K)])
+    keep = np.where(conv)[0]
+    assert conv.mean() > 0.5
+    rel = np.sqrt(np.sum((got[keep] - ref[keep]) ** 2) / np.sum(ref[keep] ** 2))
+    assert rel <= TOL_MIXED, rel
+    if conv.all():
+        assert bits == 0
+
+
+@pytest.mark.parametrize("n,cons", [(9, 7), (5, 7), (17, 3)])
+def test_mixed_1000_steps_vs_fp64(sl, n, cons):
+    """Config 2 shape (Gaussian pulse, boundary+mass[+energy]) at reduced K: after 1000 steps the
+    mixed path stays within 1e-6 relative L2 of the FP64 path (which matches the oracle to
+    1e-12 per step)."""
+    K = 4096
+    prob = sl_inputs.config2_1d_gauss(n, K)
+    c64 = sl.Context(1, K, 1, prob.box, n, 0, sl.FP64, prob.bc, prob.ghost)
+    cm = mixed_ctx(sl, K, n)
+    gv = sl.velocity(sl.VEL_CONST, 1.0)
+    dt = c64.max_dt(gv)
+    x, _ = c64.node_coords()
+    phi = torch.tensor(prob.phi0(x).ravel(), device="cuda")
+    a64, b64 = phi.clone(), torch.empty_like(phi)
+    am, bm = cm.pack(phi), cm.new_state()
+    opts = sl.options(cons, 4)
+    errs = {}
+    for s in range(1000):
+        c64.step(a64, b64, gv, s * dt, dt, opts)
+        cm.step(am, bm, gv, s * dt, dt, opts)
+        a64, b64 = b64, a64
+        am, bm = bm, am
+        if s + 1 in (1, 10, 100, 1000):
+            d = cm.unpack(am) - a64
+            errs[s + 1] = (d.norm() / a64.norm()).item()
+    assert c64.sync() == 0 and cm.sync() == 0
+    assert errs[1] <= TOL_MIXED and errs[1000] <= TOL_MIXED, errs
+    # mass is conserved by both to round-off (periodic, mass constraint)
+    assert abs(cm.mass(am) - c64.mass(a64)) < 1e-12 * abs(c64.mass(a64))
+
+
+def test_mixed_full_size_sampled(sl):
+    """Full 2^20-element configuration: sampled elements recomputed by the oracle from the GPU
+    state before the step."""
+    prob = sl_inputs.config2_1d_gauss(9)
+    cm = mixed_ctx(sl, prob.kx, 9)
+    setup = O.setup_from_problem(prob)
+    gv = sl.velocity(sl.VEL_CONST, 1.0)
+    dt = cm.max_dt(gv)
+    x, _ = cm.node_coords()
+    am = cm.pack(torch.tensor(prob.phi0(x).ravel(), device="cuda"))
+    bm = cm.new_state()
+    opts = sl.options(prob.constraints, 4)
+    for s in range(5):
+        cm.step(am, bm, gv, s * dt, dt, opts)
+        am, bm = bm, am
+    pre = cm.unpack(am).cpu().numpy().reshape(prob.kx, 9)
+    cm.step(am, bm, gv, 5 * dt, dt, opts)
+    assert cm.sync() == 0
+    got = cm.unpack(bm).cpu().numpy().reshape(prob.kx, 9)
+    K = prob.kx
+    sample = np.unique(np.concatenate([[0, K - 1], sl_inputs.sample_elements(4096, K, 3),
+                                       np.arange(K // 2 - 64, K // 2 + 64)]))
+    ref, _ = O.step_1d(setup, pre, O.StepOpts(O.Vel(O.VEL_CONST, (1.0, 0, 0, 0, 0, 0)), 5 * dt, dt,
+                                              prob.constraints, 4), elements=sample)
+    rel = np.sqrt(np.sum((got[sample] - ref[sample]) ** 2) / np.sum(ref[sample] ** 2))
+    assert rel <= 1e-9, rel
+
+
+def test_mixed_unsupported_combinations(sl):
+    cm = mixed_ctx(sl, 8, 5)
+    st, out = cm.new_state(), cm.new_state()
+    with pytest.raises(sl.SlError) as e:
+        cm.step(st, out, sl.velocity(sl.VEL_SINX), 0.0, 1e-3, sl.options(1, 4))
+    assert e.value.status == sl.SL_EUNSUPPORTED
+    with pytest.raises(sl.SlError) as e:
+        cm.step(st, out, sl.velocity(sl.VEL_CONST, 1.0), 0.0, 1e-3, sl.options(7, 4, sl.FIT_SOFT))
+    assert e.value.status == sl.SL_EUNSUPPORTED
+
+
+def test_mixed_run_host(sl):
+    cm = mixed_ctx(sl, 500, 9)
+    gv = sl.velocity(sl.VEL_CONST, 1.0)
+    dt = cm.max_dt(gv)
+    x, _ = cm.node_coords()
+    phi = 1.0 + np.sin(2 * np.pi * x)
+    hin = torch.tensor(phi.ravel()).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    cm.run_host(hin, hout, gv, 0.0, dt, 4, sl.options(7, 4))
+    a = cm.pack(hin.cuda())
+    b = cm.new_state()
+    for s in range(4):
+        cm.step(a, b, gv, s * dt, dt, sl.options(7, 4))
+        a, b = b, a
+    assert torch.equal(cm.unpack(a).cpu(), hout)
