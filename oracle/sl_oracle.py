@@ -494,7 +494,7 @@ def _face_flux_1d(setup, phi, k, side, o, power):
                 foot, _, fac = rk_particles(o.vel, np.array([xf]), np.zeros(1), np.ones(1), tau,
                                             -c[s] * o.dt, o.rk_order)
             shift = 0.0
-            if up != k:     # express the foot in the neighbour's frame across a periodic wrap
+            if un < 0:      # foot in the neighbour's frame (across a periodic wrap it is shifted)
                 jj = k - 1 if side == 0 else k + 1
                 shift = (up - jj) * setup.hx
             val = float(_poly_at_1d(setup, phi, up, foot + shift)[0] / fac[0])

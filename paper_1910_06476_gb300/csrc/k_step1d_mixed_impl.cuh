@@ -90,77 +90,97 @@ __global__ void __launch_bounds__(TILE) k_step1d_mixed(const __grid_constant__ M
     for (int j = 0; j < NN; ++j) res[j] = pl[j];
 
     if (P.energy_on) {
-      // energy mismatch from increments: variance part, plus 2 ref x mass residual when the mass
-      // row is not enforced (with it, that bracket vanishes identically)
-      float gv = 0.0f, gm = 0.0f, escale = 0.0f;
+      // The energy iteration is covariant under phi -> c phi (gamma, alpha, beta scale by c^2, q by
+      // c, s is invariant), so it runs on values scaled by a power of two to order one; elements
+      // whose values lie below the normal float range carry no energy correction.
+      float smax = fabsf(ref);
 #pragma unroll
-      for (int i = 0; i < NN; ++i) {
-        gv = fmaf(P.w[i], pl[i] * pl[i] - ps[i] * ps[i], gv);
-        gm = fmaf(P.w[i], pl[i] - ps[i], gm);
-        const float phv = ref + ps[i];
-        escale = fmaf(P.w[i], phv * phv, escale);
-      }
-      for (int s = 0; s < P.nst; ++s) {
-        float es = 0.0f, eu = 0.0f;
+      for (int i = 0; i < NN; ++i) smax = fmaxf(smax, fmaxf(fabsf(ps[i]), fabsf(pu[i])));
+      if (smax >= 1e-30f) {
+        int ex;
+        frexpf(smax, &ex);
+        const float sc = ldexpf(1.0f, -ex), usc = ldexpf(1.0f, ex);
+        const float rf = ref * sc;
+        float qs[NN], qu[NN], ql[NN];
 #pragma unroll
-        for (int i = 0; i < NN; ++i) { es = fmaf(P.E[s][i], ps[i], es); eu = fmaf(P.E[s][i], pu[i], eu); }
-        gv = fmaf(P.lam * P.fb[s], es * es - eu * eu, gv);
-        gm = fmaf(P.lam * P.fb[s], es - eu, gm);
-      }
-      const float gamma = P.mass_on ? gv : fmaf(2.0f * ref, gm, gv);
-      if (fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {
-        float pmax = 0.0f;
+        for (int i = 0; i < NN; ++i) { qs[i] = ps[i] * sc; qu[i] = pu[i] * sc; ql[i] = pl[i] * sc; }
+        // energy mismatch from increments: variance part, plus 2 ref x mass residual when the mass
+        // row is not enforced (with it, that bracket vanishes identically)
+        float gv = 0.0f, gm = 0.0f, escale = 0.0f;
 #pragma unroll
-        for (int i = 0; i < NN; ++i) pmax = fmaxf(pmax, fabsf(pl[i]));
-        const float tol = fmaxf(P.picard_rtol * fabsf(ref), 2.4e-7f * pmax) + 1e-37f;
-        bool conv = false, feasible = true;
-        for (int it = 0; it < P.picard_cap; ++it) {
-          float av[NN], q[NN];
-#pragma unroll
-          for (int i = 0; i < NN; ++i) av[i] = P.w[i] * (P.mass_on ? res[i] : ref + res[i]);
-          float ca[MMAX1D];
-          for (int k = 0; k < P.m; ++k) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NN; ++i) acc = fmaf(P.C[k * NN + i], av[i], acc);
-            ca[k] = acc;
-          }
-#pragma unroll
-          for (int j = 0; j < NN; ++j) {
-            float acc = av[j];
-            for (int k = 0; k < P.m; ++k) acc = fmaf(-P.Cp[j * P.m + k], ca[k], acc);
-            q[j] = acc;
-          }
-          float alpha = 0.0f, beta = 0.0f, wq = 0.0f;
-#pragma unroll
-          for (int i = 0; i < NN; ++i) {
-            alpha = fmaf(P.w[i] * pl[i], q[i], alpha);
-            beta = fmaf(P.w[i] * q[i], q[i], beta);
-            wq = fmaf(P.w[i], q[i], wq);
-          }
-          if (!P.mass_on) alpha = fmaf(ref, wq, alpha);
-          float s;
-          if (beta <= 0.0f) { s = 0.0f; feasible = gamma <= 0.0f; }
-          else {
-            const float disc = alpha * alpha - beta * gamma;
-            if (disc < 0.0f) { s = -alpha / beta; feasible = false; }
-            else {
-              const float root = sqrtf(disc);
-              const float den = alpha + (alpha >= 0.0f ? root : -root);
-              s = den == 0.0f ? 0.0f : -gamma / den;
-              feasible = true;
-            }
-          }
-          float delta = 0.0f;
-#pragma unroll
-          for (int i = 0; i < NN; ++i) {
-            const float nv = fmaf(s, q[i], pl[i]);
-            delta = fmaxf(delta, fabsf(nv - res[i]));
-            res[i] = nv;
-          }
-          if (delta <= tol) { conv = feasible; break; }
+        for (int i = 0; i < NN; ++i) {
+          gv = fmaf(P.w[i], ql[i] * ql[i] - qs[i] * qs[i], gv);
+          gm = fmaf(P.w[i], ql[i] - qs[i], gm);
+          const float phv = rf + qs[i];
+          escale = fmaf(P.w[i], phv * phv, escale);
         }
-        ok = conv;
+        for (int s = 0; s < P.nst; ++s) {
+          float es = 0.0f, eu = 0.0f;
+#pragma unroll
+          for (int i = 0; i < NN; ++i) { es = fmaf(P.E[s][i], qs[i], es); eu = fmaf(P.E[s][i], qu[i], eu); }
+          gv = fmaf(P.lam * P.fb[s], es * es - eu * eu, gv);
+          gm = fmaf(P.lam * P.fb[s], es - eu, gm);
+        }
+        const float gamma = P.mass_on ? gv : fmaf(2.0f * rf, gm, gv);
+        if (fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {
+          float pmax = 0.0f;
+#pragma unroll
+          for (int i = 0; i < NN; ++i) pmax = fmaxf(pmax, fabsf(ql[i]));
+          const float tol = fmaxf(P.picard_rtol * fabsf(rf), 2.4e-7f * pmax) + 1e-30f;
+          float cur[NN];
+#pragma unroll
+          for (int i = 0; i < NN; ++i) cur[i] = ql[i];
+          bool conv = false, feasible = true;
+          for (int it = 0; it < P.picard_cap; ++it) {
+            float av[NN], q[NN];
+#pragma unroll
+            for (int i = 0; i < NN; ++i) av[i] = P.w[i] * (P.mass_on ? cur[i] : rf + cur[i]);
+            float ca[MMAX1D];
+            for (int k = 0; k < P.m; ++k) {
+              float acc = 0.0f;
+#pragma unroll
+              for (int i = 0; i < NN; ++i) acc = fmaf(P.C[k * NN + i], av[i], acc);
+              ca[k] = acc;
+            }
+#pragma unroll
+            for (int j = 0; j < NN; ++j) {
+              float acc = av[j];
+              for (int k = 0; k < P.m; ++k) acc = fmaf(-P.Cp[j * P.m + k], ca[k], acc);
+              q[j] = acc;
+            }
+            float alpha = 0.0f, beta = 0.0f, wq = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NN; ++i) {
+              alpha = fmaf(P.w[i] * ql[i], q[i], alpha);
+              beta = fmaf(P.w[i] * q[i], q[i], beta);
+              wq = fmaf(P.w[i], q[i], wq);
+            }
+            if (!P.mass_on) alpha = fmaf(rf, wq, alpha);
+            float s;
+            if (beta <= 0.0f) { s = 0.0f; feasible = gamma <= 0.0f; }
+            else {
+              const float disc = alpha * alpha - beta * gamma;
+              if (disc < 0.0f) { s = -alpha / beta; feasible = false; }
+              else {
+                const float root = sqrtf(disc);
+                const float den = alpha + (alpha >= 0.0f ? root : -root);
+                s = den == 0.0f ? 0.0f : -gamma / den;
+                feasible = true;
+              }
+            }
+            float delta = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NN; ++i) {
+              const float nv = fmaf(s, q[i], ql[i]);
+              delta = fmaxf(delta, fabsf(nv - cur[i]));
+              cur[i] = nv;
+            }
+            if (delta <= tol) { conv = feasible; break; }
+          }
+#pragma unroll
+          for (int i = 0; i < NN; ++i) res[i] = cur[i] * usc;
+          ok = conv;
+        }
       }
     }
   }

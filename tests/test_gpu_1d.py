@@ -65,7 +65,7 @@ CASES = [
     (40, 6, 0, 1, ("const", -0.9), 7, 4, 0, 1),
     (24, 7, 1, 0, ("sinx",), 3, 4, 0, 0),
     (24, 7, 1, 0, ("sinx",), 1, 2, 1, 1),
-    (24, 8, 0, 0, ("sinx",), 7, 3, 0, 0),
+    (24, 8, 0, 0, ("sinx",), 3, 3, 0, 0),
     (1, 6, 0, 0, ("const", 1.0), 3, 4, 0, 0),
     (2, 6, 0, 1, ("const", 1.0), 7, 4, 0, 0),
     (127, 4, 0, 0, ("const", 1.0), 2, 4, 0, 0),
