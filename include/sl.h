@@ -21,9 +21,11 @@
  *     (ex, ey) at offset ((ey*kx + ex)*n + j)*n + i); p-adaptive 2D meshes store element e
  *     (row-major over (ey, ex)) at offset off[e] with n_e*n_e values, off being the exclusive
  *     prefix sum of n_e^2.  SL_FP64 state is one double per node.  SL_MIXED state is
- *     double-float: a plane of sl_state_size floats "hi" followed by a plane of as many floats
- *     "lo", the node value being hi + lo (about 48 significant bits); sl_pack and sl_unpack
- *     convert from and to doubles.  Either way a state buffer has sl_state_bytes bytes.
+ *     double-float: a plane of sl_state_size floats "hi" at float offset 0 and a plane of as
+ *     many floats "lo" at float offset P = sl_state_size rounded up to a multiple of 64 (so
+ *     both planes start 256-byte aligned); the node value is hi + lo (about 48 significant
+ *     bits).  sl_pack and sl_unpack convert from and to doubles.  A state buffer has
+ *     sl_state_bytes bytes (8 per node, plus the padding of the mixed format).
  *   - Pointers documented as "host" are host memory; everything else is device memory.
  *   - The library owns its tables, operators and workspace (allocated in sl_init and freed in
  *     sl_free).  All device work is enqueued on the stream given to sl_init; no call

@@ -138,7 +138,7 @@ class Context:
         self.size = int(self._lib.sl_state_size(h))
         self.shape = (kx, n) if dim == 1 else (ky, kx, n, n)
         # number of state elements of self.dtype in one state buffer (two float planes when mixed)
-        self.numel = self.size if precision == FP64 else 2 * self.size
+        self.numel = int(self._lib.sl_state_bytes(h)) // (8 if precision == FP64 else 4)
 
     def _check(self, st):
         if st != SL_OK:

@@ -10,8 +10,9 @@ constexpr int RBLOCK = 256;
 
 // PAIR = true reads the double-float state (hi plane, then lo plane) of the mixed path
 template <typename T, bool PAIR>
-__global__ void __launch_bounds__(RBLOCK) k_partial(int64_t nelem, int nper, int dim, const T* __restrict__ phi,
-                                                   const double* __restrict__ w, int power, double* partial) {
+__global__ void __launch_bounds__(RBLOCK) k_partial(int64_t nelem, int nper, int64_t plane, int dim,
+                                                   const T* __restrict__ phi, const double* __restrict__ w, int power,
+                                                   double* partial) {
   __shared__ double red[RBLOCK];
   __shared__ double ws[NMAX * NMAX];
   const int nd = dim == 1 ? nper : nper * nper;
@@ -21,7 +22,7 @@ __global__ void __launch_bounds__(RBLOCK) k_partial(int64_t nelem, int nper, int
   double acc = 0.0;
   const int64_t total = nelem * nd;
   for (int64_t idx = (int64_t)blockIdx.x * RBLOCK + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * RBLOCK) {
-    const double v = PAIR ? (double)phi[idx] + (double)phi[idx + total] : (double)phi[idx];
+    const double v = PAIR ? (double)phi[idx] + (double)phi[idx + plane] : (double)phi[idx];
     acc += ws[idx % nd] * (power == 1 ? v : v * v);
   }
   red[threadIdx.x] = acc;
@@ -51,13 +52,13 @@ __global__ void __launch_bounds__(RBLOCK) k_final(int nparts, const double* __re
 
 void launch_mass_energy_f64(int64_t nelem, int nper, const double* phi, const double* w, int dim, int power,
                             double scale, double* partial, double* result, int nblocks, cudaStream_t s) {
-  k_partial<double, false><<<nblocks, RBLOCK, 0, s>>>(nelem, nper, dim, phi, w, power, partial);
+  k_partial<double, false><<<nblocks, RBLOCK, 0, s>>>(nelem, nper, 0, dim, phi, w, power, partial);
   k_final<<<1, RBLOCK, 0, s>>>(nblocks, partial, scale, result);
 }
 
-void launch_mass_energy_pair(int64_t nelem, int nper, const float* phi, const double* w, int dim, int power,
-                             double scale, double* partial, double* result, int nblocks, cudaStream_t s) {
-  k_partial<float, true><<<nblocks, RBLOCK, 0, s>>>(nelem, nper, dim, phi, w, power, partial);
+void launch_mass_energy_pair(int64_t nelem, int nper, int64_t plane, const float* phi, const double* w, int dim,
+                             int power, double scale, double* partial, double* result, int nblocks, cudaStream_t s) {
+  k_partial<float, true><<<nblocks, RBLOCK, 0, s>>>(nelem, nper, plane, dim, phi, w, power, partial);
   k_final<<<1, RBLOCK, 0, s>>>(nblocks, partial, scale, result);
 }
 

@@ -32,31 +32,31 @@ void launch_step1d_mixed(const Mixed1DParams& p, const float* in, float* out, un
 
 namespace {
 // hi = fl(d), lo = fl(d - hi): hi + lo carries about 48 bits of d
-__global__ void k_pack(int64_t nvals, const double* __restrict__ src, float* __restrict__ dst) {
+__global__ void k_pack(int64_t nvals, int64_t plane, const double* __restrict__ src, float* __restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvals; i += (int64_t)gridDim.x * blockDim.x) {
     const double d = src[i];
     const float hi = (float)d;
     dst[i] = hi;
-    dst[nvals + i] = (float)(d - (double)hi);
+    dst[plane + i] = (float)(d - (double)hi);
   }
 }
 
-__global__ void k_unpack(int64_t nvals, const float* __restrict__ src, double* __restrict__ dst) {
+__global__ void k_unpack(int64_t nvals, int64_t plane, const float* __restrict__ src, double* __restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvals; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (double)src[i] + (double)src[nvals + i];
+    dst[i] = (double)src[i] + (double)src[plane + i];
 }
 }  // namespace
 
-void launch_pack(int64_t nvals, const double* src, float* dst, cudaStream_t s) {
+void launch_pack(int64_t nvals, int64_t plane, const double* src, float* dst, cudaStream_t s) {
   if (nvals <= 0) return;
   const int grid = (int)std::min<int64_t>((nvals + 255) / 256, 152 * 16);
-  k_pack<<<grid, 256, 0, s>>>(nvals, src, dst);
+  k_pack<<<grid, 256, 0, s>>>(nvals, plane, src, dst);
 }
 
-void launch_unpack(int64_t nvals, const float* src, double* dst, cudaStream_t s) {
+void launch_unpack(int64_t nvals, int64_t plane, const float* src, double* dst, cudaStream_t s) {
   if (nvals <= 0) return;
   const int grid = (int)std::min<int64_t>((nvals + 255) / 256, 152 * 16);
-  k_unpack<<<grid, 256, 0, s>>>(nvals, src, dst);
+  k_unpack<<<grid, 256, 0, s>>>(nvals, plane, src, dst);
 }
 
 }  // namespace sl

@@ -33,43 +33,70 @@ template <int NN>
 __global__ void __launch_bounds__(TILE) k_step1d_mixed(const __grid_constant__ Mixed1DParams P,
                                                        const float* __restrict__ in, float* __restrict__ out,
                                                        unsigned* status) {
-  __shared__ float shi[(TILE + 1) * NN];
-  __shared__ float slo[(TILE + 1) * NN];
+  constexpr int SH = 4;                     // row r of the tile lives at s[SH + r * NN + i]
+  constexpr int SMEM = (TILE + 1) * NN + 16;
+  __shared__ __align__(16) float shi[SMEM];
+  __shared__ __align__(16) float slo[SMEM];
   const int tid = threadIdx.x;
   const int K = P.K;
-  const int64_t plane = (int64_t)K * NN;
+  const int64_t plane = P.plane;            // float offset of the lo plane (multiple of 64)
   const int e0 = blockIdx.x * TILE;
-  // tile rows: left upwind -> [e0-1, e0+TILE), right upwind -> [e0, e0+TILE]
+  // tile rows: left upwind -> elements [e0-1, e0+TILE), right upwind -> [e0, e0+TILE]
   const int first = P.left_up ? e0 - 1 : e0;
-  for (int idx = tid; idx < (TILE + 1) * NN; idx += TILE) {
-    const int row = idx / NN, i = idx - row * NN;
-    const int e = wrap_elem(first + row, K, P.periodic != 0);
-    float h = 0.0f, l = 0.0f;
-    if (e >= 0) {
-      h = in[(int64_t)e * NN + i];
-      l = in[plane + (int64_t)e * NN + i];
+  // rows whose elements lie in [0, K) are contiguous in memory: one aligned 16-byte window
+  const int r_lo = max(0, -first), r_hi = min(TILE + 1, K - first);
+  {
+    const int64_t g0 = (int64_t)(first + r_lo) * NN, g1 = (int64_t)(first + r_hi) * NN;
+    const int64_t a0 = g0 & ~int64_t(3), a1 = (g1 + 3) & ~int64_t(3);   // a1 <= plane: padded
+    const int sbase = SH + r_lo * NN - (int)(g0 - a0);
+    const int nvec = (int)((a1 - a0) >> 2);
+    const float4* ih = reinterpret_cast<const float4*>(in + a0);
+    const float4* il = reinterpret_cast<const float4*>(in + plane + a0);
+    constexpr int VPT = ((TILE + 1) * NN + 8 + 4 * TILE - 1) / (4 * TILE);   // vectors per thread
+    float4 vh[VPT], vl[VPT];
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {          // issue every load before the first shared store
+      const int v = tid + k * TILE;
+      if (v < nvec) { vh[k] = __ldg(ih + v); vl[k] = __ldg(il + v); }
     }
-    shi[idx] = h;
-    slo[idx] = l;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      const int v = tid + k * TILE;
+      if (v < nvec) {
+        float* dh = shi + sbase + 4 * v;
+        float* dl = slo + sbase + 4 * v;
+        dh[0] = vh[k].x; dh[1] = vh[k].y; dh[2] = vh[k].z; dh[3] = vh[k].w;
+        dl[0] = vl[k].x; dl[1] = vl[k].y; dl[2] = vl[k].z; dl[3] = vl[k].w;
+      }
+    }
+  }
+  // the one halo row that can fall outside [0, K): periodic wrap (or none at an inflow face)
+  const int hrow = P.left_up ? 0 : r_hi;
+  const bool hfix = P.left_up ? (r_lo == 1) : (r_hi <= TILE);
+  __syncthreads();
+  if (hfix && tid < NN) {
+    const int eh = wrap_elem(first + hrow, K, P.periodic != 0);
+    shi[SH + hrow * NN + tid] = eh >= 0 ? in[(int64_t)eh * NN + tid] : 0.0f;
+    slo[SH + hrow * NN + tid] = eh >= 0 ? in[plane + (int64_t)eh * NN + tid] : 0.0f;
   }
   __syncthreads();
 
   const int e = e0 + tid;
   const bool active = e < K;
-  const int own = P.left_up ? tid + 1 : tid;
-  const int up = P.left_up ? tid : tid + 1;
+  const int own = SH + (P.left_up ? tid + 1 : tid) * NN;
+  const int up = SH + (P.left_up ? tid : tid + 1) * NN;
   const int eup = wrap_elem(P.left_up ? e - 1 : e + 1, K, P.periodic != 0);
   float res[NN];
   float ref = 0.0f;
   bool ok = true;
   if (active) {
-    ref = shi[own * NN];
+    ref = shi[own];
     float ps[NN], pu[NN];
 #pragma unroll
-    for (int i = 0; i < NN; ++i) ps[i] = (shi[own * NN + i] - ref) + slo[own * NN + i];
+    for (int i = 0; i < NN; ++i) ps[i] = (shi[own + i] - ref) + slo[own + i];
     if (eup >= 0) {
 #pragma unroll
-      for (int i = 0; i < NN; ++i) pu[i] = (shi[up * NN + i] - ref) + slo[up * NN + i];
+      for (int i = 0; i < NN; ++i) pu[i] = (shi[up + i] - ref) + slo[up + i];
     } else {
       const float g = (float)(P.ghost - (double)ref);   // ghost value at the inflow domain face
 #pragma unroll
@@ -199,8 +226,16 @@ __global__ void __launch_bounds__(TILE) k_step1d_mixed(const __grid_constant__ M
     }
   }
   __syncthreads();
+  // coalesced write-back: e0 * NN is a multiple of 4 (TILE is), and so is the lo plane offset
   const int nact = min(TILE, K - e0);
-  for (int idx = tid; idx < nact * NN; idx += TILE) {
+  const int nout = nact * NN, nv = nout >> 2;
+  float4* oh = reinterpret_cast<float4*>(out + (int64_t)e0 * NN);
+  float4* ol = reinterpret_cast<float4*>(out + plane + (int64_t)e0 * NN);
+  for (int v = tid; v < nv; v += TILE) {
+    oh[v] = reinterpret_cast<const float4*>(shi)[v];
+    ol[v] = reinterpret_cast<const float4*>(slo)[v];
+  }
+  for (int idx = 4 * nv + tid; idx < nout; idx += TILE) {
     out[(int64_t)e0 * NN + idx] = shi[idx];
     out[plane + (int64_t)e0 * NN + idx] = slo[idx];
   }

@@ -26,8 +26,11 @@ sl_status fail(sl_ctx* c, sl_status st, const std::string& msg) {
     if (e_ != cudaSuccess) return fail(ctx, SL_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// bytes of state per node: one double (SL_FP64) or a hi and a lo float (SL_MIXED)
-size_t node_bytes(const sl_ctx*) { return 8; }
+// bytes of one state buffer: nvals doubles (SL_FP64), or a hi and a lo plane of floats whose
+// lo plane starts at a 256-byte aligned float offset (SL_MIXED)
+size_t state_bytes(const sl_ctx* c) {
+  return c->precision == SL_FP64 ? (size_t)c->nvals * sizeof(double) : (size_t)2 * plane_stride(c->nvals) * sizeof(float);
+}
 
 void max_speed(const sl_ctx* c, const sl_velocity* v, double& um, double& vm) {
   const sl_mesh& M = c->mesh;
@@ -225,6 +228,7 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
       c->mix_rk = opt->rk_order;
       c->mix_fit = opt->fit;
     }
+    c->mix.plane = plane_stride(c->nvals);
     c->mix.picard_rtol = (float)P.picard_rtol;
     c->mix.picard_cap = P.picard_cap;
     launch_step1d_mixed(c->mix, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream);
@@ -239,7 +243,7 @@ sl_status sl_run_host(sl_ctx* c, const double* host_in, double* host_out, const 
                       double dt, int nsteps, const sl_options* opt) {
   if (!c) return SL_EINVAL;
   if (!host_in || !host_out || nsteps < 0) return fail(c, SL_EINVAL, "bad host buffers or step count");
-  const size_t bytes = (size_t)c->nvals * node_bytes(c);
+  const size_t bytes = state_bytes(c);
   if (!c->d_io) {
     if (cudaMalloc(&c->d_io, 2 * bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -261,7 +265,7 @@ sl_status sl_run_host(sl_ctx* c, const double* host_in, double* host_out, const 
   } else {
     SL_CUDA(c, cudaMemcpyAsync(c->d_io64, host_in, (size_t)c->nvals * sizeof(double), cudaMemcpyHostToDevice,
                                c->stream));
-    launch_pack(c->nvals, c->d_io64, (float*)a, c->stream);
+    launch_pack(c->nvals, plane_stride(c->nvals), c->d_io64, (float*)a, c->stream);
   }
   for (int s = 0; s < nsteps; ++s) {
     sl_status st = sl_step(c, a, b, vel, t0 + s * dt, dt, opt);
@@ -271,7 +275,7 @@ sl_status sl_run_host(sl_ctx* c, const double* host_in, double* host_out, const 
   if (c->precision == SL_FP64) {
     SL_CUDA(c, cudaMemcpyAsync(host_out, a, bytes, cudaMemcpyDeviceToHost, c->stream));
   } else {
-    launch_unpack(c->nvals, (const float*)a, c->d_io64, c->stream);
+    launch_unpack(c->nvals, plane_stride(c->nvals), (const float*)a, c->d_io64, c->stream);
     SL_CUDA(c, cudaMemcpyAsync(host_out, c->d_io64, (size_t)c->nvals * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));
   }
@@ -285,7 +289,7 @@ sl_status sl_pack(sl_ctx* c, const double* src, void* dst) {
   if (c->precision == SL_FP64)
     SL_CUDA(c, cudaMemcpyAsync(dst, src, (size_t)c->nvals * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   else
-    launch_pack(c->nvals, src, (float*)dst, c->stream);
+    launch_pack(c->nvals, plane_stride(c->nvals), src, (float*)dst, c->stream);
   SL_CUDA(c, cudaGetLastError());
   return SL_OK;
 }
@@ -296,7 +300,7 @@ sl_status sl_unpack(sl_ctx* c, const void* src, double* dst) {
   if (c->precision == SL_FP64)
     SL_CUDA(c, cudaMemcpyAsync(dst, src, (size_t)c->nvals * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   else
-    launch_unpack(c->nvals, (const float*)src, dst, c->stream);
+    launch_unpack(c->nvals, plane_stride(c->nvals), (const float*)src, dst, c->stream);
   SL_CUDA(c, cudaGetLastError());
   return SL_OK;
 }
@@ -311,8 +315,8 @@ static sl_status integral(sl_ctx* c, const void* phi, double* total, int power) 
     launch_mass_energy_f64(nel, c->n, (const double*)phi, c->d_tables + c->off_w, M.dim, power, hx * hy,
                            c->d_partial, c->d_result, c->red_blocks, c->stream);
   else
-    launch_mass_energy_pair(nel, c->n, (const float*)phi, c->d_tables + c->off_w, M.dim, power, hx * hy,
-                            c->d_partial, c->d_result, c->red_blocks, c->stream);
+    launch_mass_energy_pair(nel, c->n, plane_stride(c->nvals), (const float*)phi, c->d_tables + c->off_w, M.dim,
+                            power, hx * hy, c->d_partial, c->d_result, c->red_blocks, c->stream);
   SL_CUDA(c, cudaGetLastError());
   SL_CUDA(c, cudaMemcpyAsync(total, c->d_result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   SL_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -357,7 +361,7 @@ sl_status sl_max_dt(const sl_ctx* c, const sl_velocity* vel, int rule, double* d
 
 int64_t sl_state_size(const sl_ctx* c) { return c ? c->nvals : -1; }
 
-int64_t sl_state_bytes(const sl_ctx* c) { return c ? c->nvals * (int64_t)node_bytes(c) : -1; }
+int64_t sl_state_bytes(const sl_ctx* c) { return c ? (int64_t)state_bytes(c) : -1; }
 
 sl_status sl_node_coords(const sl_ctx* c, double* x, double* y) {
   if (!c || !x || (c->mesh.dim == 2 && !y)) return SL_EINVAL;

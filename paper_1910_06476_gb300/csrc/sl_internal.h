@@ -82,6 +82,7 @@ void launch_step1d_f64(int n, const StepParams& p, const Tables1D& tb, const dou
 // Kernel parameter block of the 1D shared-operator (mixed precision) step; passed by value.
 struct Mixed1DParams {
   int n, K, left_up, periodic, m, mass_on, energy_on, nst;
+  int64_t plane;                         // float offset of the lo plane in a state buffer
   double ghost;
   float lam;                             // |a| dt / h
   float picard_rtol;
@@ -97,14 +98,17 @@ struct Mixed1DParams {
 bool build_mixed1d(const sl_ctx* c, const FitOps& fit, double a, double dt, unsigned cons, int rk, int fitmode,
                    Mixed1DParams& P, std::string& err);
 void launch_step1d_mixed(const Mixed1DParams& p, const float* in, float* out, unsigned* status, cudaStream_t s);
-void launch_pack(int64_t nvals, const double* src, float* dst, cudaStream_t s);
-void launch_unpack(int64_t nvals, const float* src, double* dst, cudaStream_t s);
+void launch_pack(int64_t nvals, int64_t plane, const double* src, float* dst, cudaStream_t s);
+void launch_unpack(int64_t nvals, int64_t plane, const float* src, double* dst, cudaStream_t s);
+
+// float offset of the lo plane of a double-float state of nvals nodes: 256-byte aligned
+inline int64_t plane_stride(int64_t nvals) { return (nvals + 63) & ~int64_t(63); }
 void launch_mass_energy_f64(int64_t nelem, int nper, const double* phi, const double* w, int dim,
                             int power, double scale, double* partial, double* result, int nblocks,
                             cudaStream_t s);
-void launch_mass_energy_pair(int64_t nelem, int nper, const float* phi, const double* w, int dim,
-                             int power, double scale, double* partial, double* result, int nblocks,
-                             cudaStream_t s);
+void launch_mass_energy_pair(int64_t nelem, int nper, int64_t plane, const float* phi, const double* w,
+                             int dim, int power, double scale, double* partial, double* result,
+                             int nblocks, cudaStream_t s);
 
 }  // namespace sl
 
