@@ -183,6 +183,32 @@ sl_status sl_node_coords(const sl_ctx* ctx, double* x, double* y);
 /* Quadrature nodes and weights on [0, 1] of the context's basis for n nodes (host arrays). */
 sl_status sl_nodes_weights(const sl_ctx* ctx, int n, double* xi, double* w);
 
+/* Global integral sum_k h^d sum w (x) w phi^power of a double state, like sl_mass (power 1) and
+ * sl_energy (power 2), for callers that cannot allocate device memory when they need it: code
+ * that runs while a stream is being captured into a CUDA graph in global capture mode (where
+ * cudaMalloc is not permitted), host loops under a hard latency budget (cudaMalloc may
+ * synchronise the whole device), or applications whose memory pool owns all device memory.
+ * The paper has no counterpart; this is a service of the library.
+ *
+ * It allocates nothing and needs no context.  Inputs: phi (device) holds nelem elements of
+ * nper nodes (dim = 1) or nper x nper nodes (dim = 2) in state layout; w_host (host) holds the
+ * nper quadrature weights on [0, 1] (sl_nodes_weights); scale is h (1D) or hx*hy (2D).  Output:
+ * *total (device double) receives the integral.  Work is enqueued on cuda_stream; the call
+ * does not synchronise.  The sum is deterministic (fixed order), but ordered differently from
+ * sl_mass, so the two agree to rounding.
+ *
+ * Scratch: per-tile partial sums live in a fixed array of 65536 doubles (512 KB) in the
+ * library's device memory, which every GPU that loads the library holds until the process
+ * exits.  Inputs of more than SL_NOALLOC_MAX_VALUES values are rejected with SL_EINVAL (message
+ * in sl_last_error(NULL)).  Every call shares that array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race and must be serialised by the caller.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture begins.  Returns SL_ECUDA if
+ * the lookup or a launch fails. */
+#define SL_NOALLOC_MAX_VALUES ((int64_t)1 << 28)
+sl_status sl_integral_noalloc(const double* phi, int64_t nelem, int nper, int dim, const double* w_host,
+                              int power, double scale, double* total, void* cuda_stream);
+
 /* Last error message of the context (or of the last failed sl_init when ctx is null). */
 const char* sl_last_error(const sl_ctx* ctx);
 

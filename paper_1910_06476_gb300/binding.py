@@ -26,7 +26,7 @@ ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV = 1, 2, 4
 
 EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
            "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",
-           "sl_last_error"]
+           "sl_integral_noalloc", "sl_last_error"]
 
 
 class SlMesh(C.Structure):
@@ -75,6 +75,7 @@ def load_library(path=LIB_PATH):
     lib.sl_state_size.restype = C.c_int64
     lib.sl_node_coords.argtypes = [P, P, P]
     lib.sl_nodes_weights.argtypes = [P, C.c_int, P, P]
+    lib.sl_integral_noalloc.argtypes = [P, C.c_int64, C.c_int, C.c_int, P, C.c_int, C.c_double, P, P]
     lib.sl_last_error.argtypes = [P]
     lib.sl_last_error.restype = C.c_char_p
     for name in EXPORTS:

@@ -62,6 +62,10 @@ bool valid_velocity(const sl_ctx* c, const sl_velocity* v) {
 
 }  // namespace
 
+namespace sl {
+void set_global_error(const std::string& msg) { g_init_err = msg; }
+}  // namespace sl
+
 extern "C" {
 
 sl_status sl_init(const sl_mesh* mesh, int n, int basis, int precision, void* cuda_stream, sl_ctx** out) {
