@@ -1,0 +1,11 @@
+// Instantiations of the 2D FP64 step kernels for n = 7, 8, 9, 10.
+#include "k_step2d_impl.cuh"
+
+namespace sl {
+namespace k2d {
+template void launch_n<7>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
+template void launch_n<8>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
+template void launch_n<9>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
+template void launch_n<10>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
+}  // namespace k2d
+}  // namespace sl

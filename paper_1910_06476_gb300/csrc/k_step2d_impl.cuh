@@ -1,0 +1,508 @@
+#pragma once
+// 2D DSEM-SL step in double precision for any prescribed velocity (Sec. 4, two-dimensional
+// scheme), in two kernels with one CTA per element and one thread per particle / node.
+//
+// Phase 1 (k_p1): seed particles at the tensor Gauss nodes, integrate them with explicit RK
+// (eq. 4.4a with u and v), solve the collocation system of eq. 5.4,
+//     sum_{l,m} phihat_{ml} h_l(xi*_p) h_m(eta*_p) = phi*_p   for every particle p,
+// take the face traces of phihat (eq. 2dx_bnd_interpolate, 2dy_bnd_interpolate) and integrate
+// the outflow mass/energy flux through each face over the step (RK quadrature of the face flux,
+// the face value being this element's phi^n at the backward characteristic foot).  phihat,
+// traces and fluxes go to workspace in global memory.
+// Phase 2 (k_p2): upwind the interface values per face point (eq. 4.12a), form the mass and
+// energy targets (eq. remap_mass, remap_energy) from own and neighbour fluxes, apply the
+// constrained least-squares fit (eq. matrix_a; 4n boundary rows + mass) and the energy
+// iteration, and store phi^{n+1}.
+//
+// The collocation matrix is solved matrix-free by preconditioned iterative refinement:
+// phihat <- phihat + M^{-1} (phi* - H phihat), with M = A_y (x) A_x the exact matrix of a uniform
+// shift by the element's mean particle displacement, whose inverse is the 1D remap R_y (x) R_x.
+// H phihat costs n^2 per particle (the advected basis values are kept in registers).
+#include "sl_internal.h"
+
+namespace sl {
+namespace k2d {
+
+static __constant__ int c_rk_s[5] = {0, 1, 2, 3, 4};
+static __constant__ double c_rk_a[5][4][4] = {
+    {},
+    {{0}},
+    {{0, 0}, {1.0, 0}},
+    {{0, 0, 0}, {0.5, 0, 0}, {-1.0, 2.0, 0}},
+    {{0, 0, 0, 0}, {0.5, 0, 0, 0}, {0, 0.5, 0, 0}, {0, 0, 1.0, 0}}};
+static __constant__ double c_rk_b[5][4] = {
+    {}, {1.0}, {0.5, 0.5}, {1.0 / 6, 2.0 / 3, 1.0 / 6}, {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}};
+static __constant__ double c_rk_c[5][4] = {{}, {0.0}, {0.0, 1.0}, {0.0, 0.5, 1.0}, {0.0, 0.5, 0.5, 1.0}};
+
+constexpr int SOLVE_CAP = 60;
+constexpr double SOLVE_RTOL = 1e-15;
+
+// prescribed 2D velocity (divergence-free kinds only)
+__device__ __forceinline__ void vel2d(const StepParams& P, double x, double y, double t, double& u, double& v) {
+  switch (P.vel_kind) {
+    case SL_VEL_ROTATION:
+      u = -P.vp[0] * (y - P.vp[2]);
+      v = P.vp[0] * (x - P.vp[1]);
+      break;
+    case SL_VEL_SWIRL: {
+      const double c = cospi(t / P.vp[0]);
+      const double sx = sinpi(x), sy = sinpi(y);
+      u = sx * sx * sinpi(2.0 * y) * c;
+      v = -sy * sy * sinpi(2.0 * x) * c;
+      break;
+    }
+    default:
+      u = P.vp[0];
+      v = P.vp[1];
+  }
+}
+
+// one explicit RK step of dx/dt = u, dy/dt = v of size h (h < 0 runs the characteristic back)
+__device__ __forceinline__ void rk2d(const StepParams& P, double& x, double& y, double t, double h) {
+  if (P.vel_kind == SL_VEL_CONST) {
+    x += h * P.vp[0];
+    y += h * P.vp[1];
+    return;
+  }
+  const int S = c_rk_s[P.rk];
+  double kx[4], ky[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s < S) {
+      double xs = x, ys = y;
+#pragma unroll
+      for (int j = 0; j < s; ++j) {
+        xs += h * c_rk_a[P.rk][s][j] * kx[j];
+        ys += h * c_rk_a[P.rk][s][j] * ky[j];
+      }
+      vel2d(P, xs, ys, t + c_rk_c[P.rk][s] * h, kx[s], ky[s]);
+    }
+  }
+  double sx = 0.0, sy = 0.0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (s < S) {
+      sx += c_rk_b[P.rk][s] * kx[s];
+      sy += c_rk_b[P.rk][s] * ky[s];
+    }
+  x += h * sx;
+  y += h * sy;
+}
+
+// Lagrange basis on the fixed nodes at z: out_l = lam_l prod_{k != l} (z - xi_k)
+template <int NN>
+__device__ __forceinline__ void basis_at(const double* xi, const double* lam, double z, double* out) {
+  double d[NN], pre[NN];
+#pragma unroll
+  for (int k = 0; k < NN; ++k) d[k] = z - xi[k];
+  double acc = 1.0;
+#pragma unroll
+  for (int k = 0; k < NN; ++k) { pre[k] = acc; acc *= d[k]; }
+  double suf = 1.0;
+#pragma unroll
+  for (int l = NN - 1; l >= 0; --l) {
+    out[l] = lam[l] * pre[l] * suf;
+    suf *= d[l];
+  }
+}
+
+// deterministic block reductions (fixed tree order); every thread gets the result
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  __syncthreads();
+  if (ln == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s += red[i];
+  return s;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  __syncthreads();
+  if (ln == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s = fmax(s, red[i]);
+  return s;
+}
+
+template <int NN>
+struct Shape {
+  static constexpr int ND = NN * NN;
+  static constexpr int NT = ((ND > 4 * NN ? ND : 4 * NN) + 31) / 32 * 32;   // threads per CTA
+};
+
+struct Work2D {            // workspace between the two phases
+  double* phihat;          // [nel][n^2]
+  double* traces;          // [nel][4][n]   faces W, E, S, N at the tangential nodes
+  double* fluxes;          // [nel][4][2]   outflow (mass, energy) flux per face over the step
+};
+
+__device__ __forceinline__ int nb_index(const StepParams& P, int ex, int ey, int face, bool& wrapped) {
+  int jx = ex + (face == 0 ? -1 : face == 1 ? 1 : 0);
+  int jy = ey + (face == 2 ? -1 : face == 3 ? 1 : 0);
+  wrapped = false;
+  if (jx >= 0 && jx < P.kx && jy >= 0 && jy < P.ky) return jy * P.kx + jx;
+  if (P.bc[face] != SL_BC_PERIODIC) return -1;
+  wrapped = true;
+  jx = (jx + P.kx) % P.kx;
+  jy = (jy + P.ky) % P.ky;
+  return jy * P.kx + jx;
+}
+
+template <int NN>
+__global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, Tables1D tb, const double* __restrict__ in,
+                                                     Work2D W, unsigned* status) {
+  constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
+  __shared__ double s_xi[NN], s_lam[NN], s_w[NN], s_l0[NN], s_l1[NN];
+  __shared__ double s_phi[ND], s_ph[ND], s_t[ND], s_r[ND];
+  __shared__ double s_Rx[ND], s_Ry[ND];
+  __shared__ double s_red[NT / 32];
+  __shared__ double s_face[4][NN][2];
+  const int tid = threadIdx.x;
+  const int e = blockIdx.x;
+  const int ex = e % P.kx, ey = e / P.kx;
+  const double hx = P.hx, hy = P.hy;
+  const double x0 = P.x0 + ex * hx, y0 = P.y0 + ey * hy;
+  if (tid < NN) {
+    s_xi[tid] = tb.xi[tid]; s_lam[tid] = tb.lam[tid]; s_w[tid] = tb.w[tid];
+    s_l0[tid] = tb.l0[tid]; s_l1[tid] = tb.l1[tid];
+  }
+  const bool part = tid < ND;
+  const int i = tid % NN, j = tid / NN;
+  if (part) s_phi[tid] = in[(size_t)e * ND + tid];
+  __syncthreads();
+
+  // (a)-(b) seed and advect the particle of node (i, j)
+  double Lx[NN], Ly[NN], phs = 0.0, dxs = 0.0, dys = 0.0;
+  if (part) {
+    double x = x0 + hx * s_xi[i], y = y0 + hy * s_xi[j];
+    rk2d(P, x, y, P.t, P.dt);
+    const double xs = (x - x0) / hx, ys = (y - y0) / hy;
+    basis_at<NN>(s_xi, s_lam, xs, Lx);
+    basis_at<NN>(s_xi, s_lam, ys, Ly);
+    phs = s_phi[tid];                       // divergence-free velocity: phi* = phi^n
+    dxs = xs - s_xi[i];
+    dys = ys - s_xi[j];
+  }
+  const double mdx = block_sum<NT>(dxs, s_red) / ND;
+  const double mdy = block_sum<NT>(dys, s_red) / ND;
+  // 1D remap operators of the mean shift: R[l][q] = h_q(xi_l - shift)
+  if (part) {
+    double b[NN];
+    basis_at<NN>(s_xi, s_lam, s_xi[j] - mdx, b);
+    s_Rx[tid] = b[i];                        // row l = j, column q = i
+    basis_at<NN>(s_xi, s_lam, s_xi[j] - mdy, b);
+    s_Ry[tid] = b[i];
+    s_r[tid] = phs;
+  }
+  __syncthreads();
+  // apply M^{-1} = R_y (x) R_x to s_r, add into s_ph (init = 0 on the first call)
+  auto precond_add = [&](bool first) {
+    if (part) {                              // t[j][l] = sum_q Rx[l][q] r[j][q]   (thread: j, l = i)
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < NN; ++q) acc += s_Rx[i * NN + q] * s_r[j * NN + q];
+      s_t[tid] = acc;
+    }
+    __syncthreads();
+    if (part) {                              // out[m][l] = sum_q Ry[m][q] t[q][l] (thread: m = j, l = i)
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < NN; ++q) acc += s_Ry[j * NN + q] * s_t[q * NN + i];
+      s_ph[tid] = first ? acc : s_ph[tid] + acc;
+    }
+    __syncthreads();
+  };
+  precond_add(true);
+  const double scale = block_max<NT>(part ? fabs(phs) : 0.0, s_red);
+  bool solved = false;
+  for (int it = 0; it < SOLVE_CAP; ++it) {
+    double r = 0.0;
+    if (part) {                              // residual at the particle: phi* - sum Ly_m Lx_l phihat_ml
+      double acc = 0.0;
+#pragma unroll 1
+      for (int mm = 0; mm < NN; ++mm) {
+        double row = 0.0;
+#pragma unroll
+        for (int l = 0; l < NN; ++l) row += s_ph[mm * NN + l] * Lx[l];
+        acc += Ly[mm] * row;
+      }
+      r = phs - acc;
+      s_r[tid] = r;
+    }
+    const double rmax = block_max<NT>(fabs(r), s_red);
+    if (rmax <= SOLVE_RTOL * scale || rmax == 0.0) { solved = true; break; }
+    precond_add(false);
+  }
+  if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);
+  if (part) W.phihat[(size_t)e * ND + tid] = s_ph[tid];
+
+  // traces of phihat at the four faces, thread (face, q)
+  if (tid < 4 * NN) {
+    const int f = tid / NN, q = tid % NN;
+    const double* L = (f == 1 || f == 3) ? s_l1 : s_l0;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NN; ++k) acc += (f < 2 ? s_ph[q * NN + k] : s_ph[k * NN + q]) * L[k];
+    W.traces[(size_t)e * 4 * NN + tid] = acc;
+  }
+  // outflow fluxes: for each face point and RK stage where u.n_out > TIE, phi^n at the foot
+  if (P.cons & (SL_C_MASS | SL_C_ENERGY)) {
+    double fm = 0.0, fe = 0.0;
+    if (tid < 4 * NN) {
+      const int f = tid / NN, q = tid % NN;
+      const double xf = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
+      const double yf = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
+      const double nx = f == 0 ? -1.0 : f == 1 ? 1.0 : 0.0, ny = f == 2 ? -1.0 : f == 3 ? 1.0 : 0.0;
+      const double Wq = (f < 2 ? hy : hx) * s_w[q];
+      const int S = c_rk_s[P.rk];
+      for (int s = 0; s < S; ++s) {
+        const double cs = c_rk_c[P.rk][s];
+        const double tau = P.t + cs * P.dt;
+        double u, v;
+        vel2d(P, xf, yf, tau, u, v);
+        const double un = u * nx + v * ny;
+        if (un > TIE) {
+          double fx = xf, fy = yf;
+          if (cs != 0.0) rk2d(P, fx, fy, tau, -cs * P.dt);
+          double bx[NN], by[NN];
+          basis_at<NN>(s_xi, s_lam, (fx - x0) / hx, bx);
+          basis_at<NN>(s_xi, s_lam, (fy - y0) / hy, by);
+          double val = 0.0;
+#pragma unroll 1
+          for (int mm = 0; mm < NN; ++mm) {
+            double row = 0.0;
+#pragma unroll
+            for (int l = 0; l < NN; ++l) row += s_phi[mm * NN + l] * bx[l];
+            val += by[mm] * row;
+          }
+          const double bw = c_rk_b[P.rk][s] * Wq * un;
+          fm += bw * val;
+          fe += bw * val * val;
+        }
+      }
+      s_face[f][q][0] = fm;
+      s_face[f][q][1] = fe;
+    }
+    __syncthreads();
+    if (tid < 8) {                           // per face, sum over the points in index order
+      const int f = tid >> 1, k = tid & 1;
+      double acc = 0.0;
+      for (int q = 0; q < NN; ++q) acc += s_face[f][q][k];
+      W.fluxes[(size_t)e * 8 + tid] = acc;
+    }
+  }
+}
+
+template <int NN>
+__global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, Tables1D tb, const double* __restrict__ in,
+                                                     Work2D W, double* __restrict__ out, unsigned* status) {
+  constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
+  constexpr int MMAX = 4 * NN + 1;
+  __shared__ double s_xi[NN], s_w[NN], s_l0[NN], s_l1[NN];
+  __shared__ double s_ph[ND], s_a[ND];
+  __shared__ double s_r[MMAX], s_d[MMAX], s_ca[MMAX];
+  __shared__ double s_red[NT / 32];
+  const int tid = threadIdx.x;
+  const int e = blockIdx.x;
+  const int ex = e % P.kx, ey = e / P.kx;
+  const double hx = P.hx, hy = P.hy;
+  const double x0 = P.x0 + ex * hx, y0 = P.y0 + ey * hy;
+  const double tn1 = P.t + P.dt;
+  if (tid < NN) { s_xi[tid] = tb.xi[tid]; s_w[tid] = tb.w[tid]; s_l0[tid] = tb.l0[tid]; s_l1[tid] = tb.l1[tid]; }
+  const bool part = tid < ND;
+  const int i = tid % NN, j = tid / NN;
+  double phn = 0.0, ph = 0.0;
+  if (part) {
+    phn = in[(size_t)e * ND + tid];
+    ph = W.phihat[(size_t)e * ND + tid];
+    s_ph[tid] = ph;
+  }
+  __syncthreads();
+  const double w2 = part ? s_w[i] * s_w[j] : 0.0;
+  const bool bnd = (P.cons & SL_C_BOUNDARY) != 0;
+  const int nb_rows = bnd ? 4 * NN : 0;
+  // upwinded interface values (rows W, E, S, N at the tangential nodes); residual d - C phihat
+  if (bnd && tid < 4 * NN) {
+    const int f = tid / NN, q = tid % NN;
+    bool wr;
+    const int nb = nb_index(P, ex, ey, f, wr);
+    const int fo = f ^ 1;                    // opposite face of the neighbour
+    const double own = W.traces[(size_t)e * 4 * NN + tid];
+    const double other = nb >= 0 ? W.traces[(size_t)nb * 4 * NN + fo * NN + q] : P.ghost;
+    const double xf = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
+    const double yf = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
+    double u, v;
+    vel2d(P, xf, yf, tn1, u, v);
+    const double un = f == 0 ? -u : f == 1 ? u : f == 2 ? -v : v;
+    double val;
+    if (un > TIE) val = own;
+    else if (un < -TIE) val = other;
+    else val = nb < 0 ? own : 0.5 * (own + other);
+    s_d[tid] = val;
+    s_r[tid] = val - own;                     // the row's value at phihat is exactly the own trace
+  }
+  // mass and energy targets (reference measure)
+  double Et = 0.0;
+  const bool mass = (P.cons & SL_C_MASS) != 0, energy = (P.cons & SL_C_ENERGY) != 0;
+  if (mass || energy) {
+    double netm = 0.0, nete = 0.0;
+    if (tid == 0) {
+      for (int f = 0; f < 4; ++f) {
+        bool wr;
+        const int nb = nb_index(P, ex, ey, f, wr);
+        netm += W.fluxes[(size_t)e * 8 + 2 * f];
+        nete += W.fluxes[(size_t)e * 8 + 2 * f + 1];
+        if (nb >= 0) {
+          netm -= W.fluxes[(size_t)nb * 8 + 2 * (f ^ 1)];
+          nete -= W.fluxes[(size_t)nb * 8 + 2 * (f ^ 1) + 1];
+        } else {                              // inflow from the ghost value at a domain face
+          for (int q = 0; q < NN; ++q) {
+            const double xf = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
+            const double yf = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
+            const double Wq = (f < 2 ? hy : hx) * s_w[q];
+            for (int s = 0; s < c_rk_s[P.rk]; ++s) {
+              double u, v;
+              vel2d(P, xf, yf, P.t + c_rk_c[P.rk][s] * P.dt, u, v);
+              const double un = f == 0 ? -u : f == 1 ? u : f == 2 ? -v : v;
+              if (un < -TIE) {
+                netm += c_rk_b[P.rk][s] * Wq * un * P.ghost;
+                nete += c_rk_b[P.rk][s] * Wq * un * P.ghost * P.ghost;
+              }
+            }
+          }
+        }
+      }
+      s_a[0] = netm;
+      s_a[1] = nete;
+    }
+    __syncthreads();
+    netm = s_a[0];
+    nete = s_a[1];
+    __syncthreads();
+    const double area = hx * hy;
+    const double Mn = block_sum<NT>(w2 * phn, s_red);
+    const double En = block_sum<NT>(w2 * phn * phn, s_red);
+    if (mass) {
+      const double Mh = block_sum<NT>(w2 * ph, s_red);
+      if (tid == 0) {
+        s_d[nb_rows] = Mn - P.dt / area * netm;
+        s_r[nb_rows] = s_d[nb_rows] - Mh;
+      }
+    }
+    Et = En - P.dt / area * nete;
+  }
+  __syncthreads();
+  const int m = P.m;
+  // linear constrained fit
+  double phL = ph;
+  if (part) {
+    if (P.fit == SL_FIT_HARD) {
+      double acc = ph;
+      for (int k = 0; k < m; ++k) acc += tb.Cpinv[(size_t)tid * m + k] * s_r[k];
+      phL = acc;
+    } else {
+      double acc = 0.0;
+      for (int k = 0; k < ND; ++k) acc += tb.S[(size_t)tid * ND + k] * s_ph[k];
+      for (int k = 0; k < m; ++k) acc += tb.SCt[(size_t)tid * m + k] * s_d[k];
+      phL = acc;
+    }
+  }
+  double cur = phL;
+  bool ok = true;
+  if (energy) {
+    const double EL = block_sum<NT>(w2 * phL * phL, s_red);
+    const double gamma = EL - Et;
+    const double pmax = block_max<NT>(part ? fabs(ph) : 0.0, s_red);
+    const bool apply = fabs(gamma) > ENERGY_SKIP_RTOL * fmax(fabs(Et), EL);
+    if (apply) {
+      const double tol = P.picard_rtol * fmax(pmax, 1e-300);
+      bool conv = false, feasible = true;
+      for (int it = 0; it < P.picard_cap; ++it) {
+        const double a = w2 * cur;
+        if (part) s_a[tid] = a;
+        __syncthreads();
+        double q = 0.0;
+        if (P.fit == SL_FIT_HARD) {
+          // C a: boundary rows (traces of a), then the mass row
+          if (bnd && tid < 4 * NN) {
+            const int f = tid / NN, qq = tid % NN;
+            const double* L = (f == 1 || f == 3) ? s_l1 : s_l0;
+            double acc = 0.0;
+            for (int k = 0; k < NN; ++k) acc += (f < 2 ? s_a[qq * NN + k] : s_a[k * NN + qq]) * L[k];
+            s_ca[tid] = acc;
+          }
+          if (mass) {
+            const double cm = block_sum<NT>(w2 * a, s_red);
+            if (tid == 0) s_ca[nb_rows] = cm;
+          }
+          __syncthreads();
+          if (part) {
+            double acc = a;
+            for (int k = 0; k < m; ++k) acc -= tb.Cpinv[(size_t)tid * m + k] * s_ca[k];
+            q = acc;
+          }
+          const double alpha = block_sum<NT>(w2 * phL * q, s_red);
+          const double beta = block_sum<NT>(w2 * q * q, s_red);
+          double s;
+          if (beta <= 0.0) { s = 0.0; feasible = gamma <= 0.0; }
+          else {
+            const double disc = alpha * alpha - beta * gamma;
+            if (disc < 0.0) { s = -alpha / beta; feasible = false; }
+            else {
+              const double root = sqrt(disc);
+              const double den = alpha + (alpha >= 0.0 ? root : -root);
+              s = den == 0.0 ? 0.0 : -gamma / den;
+              feasible = true;
+            }
+          }
+          const double nv = part ? phL + s * q : 0.0;
+          const double delta = block_max<NT>(part ? fabs(nv - cur) : 0.0, s_red);
+          cur = nv;
+          if (delta < tol) { conv = feasible; break; }
+        } else {
+          if (part) {
+            double acc = 0.0;
+            for (int k = 0; k < ND; ++k) acc += tb.S[(size_t)tid * ND + k] * s_a[k];
+            q = acc;
+          }
+          const double aphi = block_sum<NT>(a * phL, s_red);
+          const double aq = block_sum<NT>(a * q, s_red);
+          const double s = (Et - aphi) / (1.0 + aq);
+          const double nv = part ? phL + s * q : 0.0;
+          const double delta = block_max<NT>(part ? fabs(nv - cur) : 0.0, s_red);
+          cur = nv;
+          if (delta < tol) { conv = true; break; }
+        }
+        __syncthreads();
+      }
+      ok = conv;
+    }
+  }
+  if (part) {
+    out[(size_t)e * ND + tid] = cur;
+    if (!isfinite(cur)) atomicOr(status, SL_ST_NONFINITE);
+  }
+  if (!ok && tid == 0) atomicOr(status, SL_ST_PICARD_NOCONV);
+}
+
+template <int NN>
+void launch_n(const StepParams& p, const Tables1D& tb, const double* in, double* out, Work2D w, unsigned* st,
+              cudaStream_t s) {
+  const int nel = p.kx * p.ky;
+  k_p1<NN><<<nel, Shape<NN>::NT, 0, s>>>(p, tb, in, w, st);
+  k_p2<NN><<<nel, Shape<NN>::NT, 0, s>>>(p, tb, in, w, out, st);
+}
+
+}  // namespace k2d
+}  // namespace sl

@@ -138,6 +138,7 @@ sl_status sl_init(const sl_mesh* mesh, int n, int basis, int precision, void* cu
     }
   c->red_blocks = 2 * 152;
   if (cudaMalloc(&c->d_tables, host.size() * sizeof(double)) != cudaSuccess ||
+      (mesh->dim == 2 && cudaMalloc(&c->d_work, work2d_doubles(nel, n) * sizeof(double)) != cudaSuccess) ||
       cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&c->d_partial, c->red_blocks * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_result, sizeof(double)) != cudaSuccess) {
@@ -163,6 +164,7 @@ void sl_free(sl_ctx* c) {
   cudaFree(c->d_result);
   cudaFree(c->d_io);
   cudaFree(c->d_io64);
+  cudaFree(c->d_work);
   delete c;
 }
 
@@ -236,6 +238,12 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
     c->mix.picard_rtol = (float)P.picard_rtol;
     c->mix.picard_cap = P.picard_cap;
     launch_step1d_mixed(c->mix, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream);
+  } else if (M.dim == 2 && c->precision == SL_FP64) {
+    if (opt->bvalue != SL_BV_INTERP)
+      return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
+    Tables1D tb{T + c->off_xi, T + c->off_w, T + c->off_lam, T + c->off_l0, T + c->off_l1,
+                T + off[0], T + off[1], T + off[2]};
+    launch_step2d_f64(c->n, P, tb, (const double*)phi_in, (double*)phi_out, c->d_work, c->d_status, c->stream);
   } else {
     return fail(c, SL_EUNSUPPORTED, "this dimension/precision combination is not built yet");
   }

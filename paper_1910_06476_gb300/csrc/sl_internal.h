@@ -79,6 +79,11 @@ struct StepParams {
 void launch_step1d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in,
                        double* out, unsigned* status, cudaStream_t s);
 
+// 2D FP64 step (two kernels); work holds nel * (n^2 + 4n + 8) doubles
+void launch_step2d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in, double* out, double* work,
+                       unsigned* status, cudaStream_t s);
+inline int64_t work2d_doubles(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 8); }
+
 // Kernel parameter block of the 1D shared-operator (mixed precision) step; passed by value.
 struct Mixed1DParams {
   int n, K, left_up, periodic, m, mass_on, energy_on, nst;
@@ -132,6 +137,7 @@ struct sl_ctx {
   int red_blocks = 0;
   void* d_io = nullptr;                  // device buffers for sl_run_host
   double* d_io64 = nullptr;
+  double* d_work = nullptr;              // 2D workspace between the two phases
   // cached shared operator of the mixed 1D path, keyed on (a, dt, constraints, rk, fit)
   bool mix_valid = false;
   double mix_a = 0, mix_dt = 0;
