@@ -1,0 +1,486 @@
+#pragma once
+// 2D DSEM-SL step in mixed precision for any prescribed velocity: double-float state, float
+// arithmetic on increments relative to a per-element reference value (Sec. 4, two-dimensional
+// scheme).  Same two phases as the FP64 kernels (k_step2d_impl.cuh):
+//   phase 1: advect the particles in element-local coordinates (float), solve the collocation
+//            system of eq. 5.4 for the increments psi = phi - ref by preconditioned iterative
+//            refinement, take the face traces, and integrate per face over the step
+//              U_out, U_in : RK/Gauss quadrature of u.n_out split by its sign,
+//              Psi, Psi2   : the same of u.n psi and u.n psi^2 at the feet of the outflow points;
+//   phase 2: interface values, mass and energy targets, constrained fit, energy iteration.
+// Everything a target needs is assembled from increments: the net mass flux of element e is
+//   ref_e (U_out + U_in)  +  sum_f (ref_nb - ref_e) U_in,f  +  sum_f (Psi_out,f - Psi'_f),
+// Psi'_f being the neighbour's outflow flux through the shared face, so float rounding scales
+// with the variation of the data instead of |phi|.  The result is written back exactly as
+// ref + psi (TwoSum).
+#include "sl_internal.h"
+
+namespace sl {
+namespace k2m {
+
+static __constant__ int c_rk_s[5] = {0, 1, 2, 3, 4};
+static __constant__ float c_rk_a[5][4][4] = {
+    {},
+    {{0}},
+    {{0, 0}, {1.0f, 0}},
+    {{0, 0, 0}, {0.5f, 0, 0}, {-1.0f, 2.0f, 0}},
+    {{0, 0, 0, 0}, {0.5f, 0, 0, 0}, {0, 0.5f, 0, 0}, {0, 0, 1.0f, 0}}};
+static __constant__ float c_rk_b[5][4] = {
+    {}, {1.0f}, {0.5f, 0.5f}, {1.0f / 6, 2.0f / 3, 1.0f / 6}, {1.0f / 6, 1.0f / 3, 1.0f / 3, 1.0f / 6}};
+static __constant__ float c_rk_c[5][4] = {{}, {0.0f}, {0.0f, 1.0f}, {0.0f, 0.5f, 1.0f}, {0.0f, 0.5f, 0.5f, 1.0f}};
+
+constexpr int SOLVE_CAP = 40;
+constexpr float SOLVE_RTOL = 3e-7f;
+
+// velocity divided by the element size: the time derivative of the reference coordinates
+__device__ __forceinline__ void vel_ref(const StepParams& P, const Mixed2DExtra& X, float x, float y, float tT,
+                                        float& u, float& v) {
+  switch (P.vel_kind) {
+    case SL_VEL_ROTATION:
+      u = -X.om * (y - X.cy) * X.ihx;
+      v = X.om * (x - X.cx) * X.ihy;
+      break;
+    case SL_VEL_SWIRL: {
+      const float c = cospif(tT);
+      const float sx = sinpif(x), sy = sinpif(y);
+      u = sx * sx * sinpif(2.0f * y) * c * X.ihx;
+      v = -sy * sy * sinpif(2.0f * x) * c * X.ihy;
+      break;
+    }
+    default:
+      u = X.a * X.ihx;
+      v = X.b * X.ihy;
+  }
+}
+
+// one RK step of the reference coordinates (xi, eta) of a point of the element with origin
+// (x0, y0); tT = t / T (swirl), h = step in time, hT = h / T
+__device__ __forceinline__ void rk_ref(const StepParams& P, const Mixed2DExtra& X, float x0, float y0, float& xi,
+                                       float& eta, float tT, float h, float hT) {
+  const int S = c_rk_s[P.rk];
+  float kx[4], ky[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s < S) {
+      float xs = xi, ys = eta;
+#pragma unroll
+      for (int j = 0; j < s; ++j) {
+        xs = fmaf(h * c_rk_a[P.rk][s][j], kx[j], xs);
+        ys = fmaf(h * c_rk_a[P.rk][s][j], ky[j], ys);
+      }
+      vel_ref(P, X, fmaf(X.hx, xs, x0), fmaf(X.hy, ys, y0), fmaf(c_rk_c[P.rk][s], hT, tT), kx[s], ky[s]);
+    }
+  }
+  float sx = 0.0f, sy = 0.0f;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (s < S) {
+      sx = fmaf(c_rk_b[P.rk][s], kx[s], sx);
+      sy = fmaf(c_rk_b[P.rk][s], ky[s], sy);
+    }
+  xi = fmaf(h, sx, xi);
+  eta = fmaf(h, sy, eta);
+}
+
+template <int NN>
+__device__ __forceinline__ void basis_at(const float* xi, const float* lam, float z, float* out) {
+  float d[NN], pre[NN];
+#pragma unroll
+  for (int k = 0; k < NN; ++k) d[k] = z - xi[k];
+  float acc = 1.0f;
+#pragma unroll
+  for (int k = 0; k < NN; ++k) { pre[k] = acc; acc *= d[k]; }
+  float suf = 1.0f;
+#pragma unroll
+  for (int l = NN - 1; l >= 0; --l) {
+    out[l] = lam[l] * pre[l] * suf;
+    suf *= d[l];
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  __syncthreads();
+  if (ln == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s += red[i];
+  return s;
+}
+
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  __syncthreads();
+  if (ln == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) s = fmaxf(s, red[i]);
+  return s;
+}
+
+template <int NN>
+struct Shape {
+  static constexpr int ND = NN * NN;
+  static constexpr int NT = ((ND > 4 * NN ? ND : 4 * NN) + 31) / 32 * 32;
+};
+
+// workspace (floats) per element: psihat [n^2], traces [4n], face sums [4][4] (U_out, U_in, Psi,
+// Psi2), element sums [4] (ref, sum w psi, sum w psi^2, unused)
+struct Work2M {
+  float* psihat;
+  float* traces;
+  float* faces;
+  float* elem;
+};
+
+__device__ __forceinline__ int nb_index(const StepParams& P, int ex, int ey, int face) {
+  int jx = ex + (face == 0 ? -1 : face == 1 ? 1 : 0);
+  int jy = ey + (face == 2 ? -1 : face == 3 ? 1 : 0);
+  if (jx >= 0 && jx < P.kx && jy >= 0 && jy < P.ky) return jy * P.kx + jx;
+  if (P.bc[face] != SL_BC_PERIODIC) return -1;
+  jx = (jx + P.kx) % P.kx;
+  jy = (jy + P.ky) % P.ky;
+  return jy * P.kx + jx;
+}
+
+template <int NN>
+__global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid_constant__ Mixed2DExtra X,
+                                                     const float* __restrict__ in, Work2M W, unsigned* status) {
+  constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
+  __shared__ float s_xi[NN], s_lam[NN], s_w[NN], s_l0[NN], s_l1[NN];
+  __shared__ float s_psi[ND], s_ph[ND], s_t[ND], s_r[ND], s_Rx[ND], s_Ry[ND];
+  __shared__ float s_red[NT / 32];
+  __shared__ float s_face[4][NN][4];
+  const int tid = threadIdx.x;
+  const int e = blockIdx.x;
+  const int ex = e % P.kx, ey = e / P.kx;
+  const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
+  if (tid < NN) {
+    s_xi[tid] = X.xi[tid]; s_lam[tid] = X.lam[tid]; s_w[tid] = X.w[tid];
+    s_l0[tid] = X.l0[tid]; s_l1[tid] = X.l1[tid];
+  }
+  const bool part = tid < ND;
+  const int i = tid % NN, j = tid / NN;
+  const float ref = in[(size_t)e * ND];
+  if (part) s_psi[tid] = (in[(size_t)e * ND + tid] - ref) + in[X.plane + (size_t)e * ND + tid];
+  __syncthreads();
+
+  // advect the particle of node (i, j) in reference coordinates
+  float Lx[NN], Ly[NN], ps = 0.0f, dxs = 0.0f, dys = 0.0f;
+  if (part) {
+    float xs = s_xi[i], ys = s_xi[j];
+    rk_ref(P, X, x0, y0, xs, ys, X.tT, X.dt, X.dtT);
+    basis_at<NN>(s_xi, s_lam, xs, Lx);
+    basis_at<NN>(s_xi, s_lam, ys, Ly);
+    ps = s_psi[tid];
+    dxs = xs - s_xi[i];
+    dys = ys - s_xi[j];
+  }
+  const float mdx = block_sum<NT>(dxs, s_red) / ND;
+  const float mdy = block_sum<NT>(dys, s_red) / ND;
+  if (part) {
+    float b[NN];
+    basis_at<NN>(s_xi, s_lam, s_xi[j] - mdx, b);
+    s_Rx[tid] = b[i];
+    basis_at<NN>(s_xi, s_lam, s_xi[j] - mdy, b);
+    s_Ry[tid] = b[i];
+    s_r[tid] = ps;
+  }
+  __syncthreads();
+  auto precond_add = [&](bool first) {
+    if (part) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NN; ++q) acc = fmaf(s_Rx[i * NN + q], s_r[j * NN + q], acc);
+      s_t[tid] = acc;
+    }
+    __syncthreads();
+    if (part) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NN; ++q) acc = fmaf(s_Ry[j * NN + q], s_t[q * NN + i], acc);
+      s_ph[tid] = first ? acc : s_ph[tid] + acc;
+    }
+    __syncthreads();
+  };
+  precond_add(true);
+  const float scale = block_max<NT>(part ? fabsf(ps) : 0.0f, s_red);
+  bool solved = false;
+  for (int it = 0; it < SOLVE_CAP; ++it) {
+    float r = 0.0f;
+    if (part) {
+      float acc = 0.0f;
+#pragma unroll 1
+      for (int mm = 0; mm < NN; ++mm) {
+        float row = 0.0f;
+#pragma unroll
+        for (int l = 0; l < NN; ++l) row = fmaf(s_ph[mm * NN + l], Lx[l], row);
+        acc = fmaf(Ly[mm], row, acc);
+      }
+      r = ps - acc;
+      s_r[tid] = r;
+    }
+    const float rmax = block_max<NT>(fabsf(r), s_red);
+    if (rmax <= SOLVE_RTOL * scale || rmax == 0.0f) { solved = true; break; }
+    precond_add(false);
+  }
+  if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);
+  if (part) W.psihat[(size_t)e * ND + tid] = s_ph[tid];
+  // element sums of psi^n (reference measure)
+  const float w2 = part ? s_w[i] * s_w[j] : 0.0f;
+  const float m1 = block_sum<NT>(w2 * ps, s_red);
+  const float m2 = block_sum<NT>(w2 * ps * ps, s_red);
+  if (tid == 0) {
+    W.elem[(size_t)e * 4 + 0] = ref;
+    W.elem[(size_t)e * 4 + 1] = m1;
+    W.elem[(size_t)e * 4 + 2] = m2;
+    W.elem[(size_t)e * 4 + 3] = 0.0f;
+  }
+  // traces of psihat (relative to ref)
+  if (tid < 4 * NN) {
+    const int f = tid / NN, q = tid % NN;
+    const float* L = (f == 1 || f == 3) ? s_l1 : s_l0;
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NN; ++k) acc = fmaf(f < 2 ? s_ph[q * NN + k] : s_ph[k * NN + q], L[k], acc);
+    W.traces[(size_t)e * 4 * NN + tid] = acc;
+  }
+  // face sums over the step
+  if (P.cons & (SL_C_MASS | SL_C_ENERGY)) {
+    if (tid < 4 * NN) {
+      const int f = tid / NN, q = tid % NN;
+      const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : s_xi[q];
+      const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : s_xi[q];
+      const float hn = f < 2 ? X.hx : X.hy;          // velocity in reference units times this = u.n
+      const float sg = (f == 0 || f == 2) ? -1.0f : 1.0f;
+      const float Wq = (f < 2 ? X.hy : X.hx) * s_w[q];
+      float uo = 0.0f, ui = 0.0f, p1 = 0.0f, p2 = 0.0f;
+      const int S = c_rk_s[P.rk];
+      for (int s = 0; s < S; ++s) {
+        const float cs = c_rk_c[P.rk][s];
+        float ur, vr;
+        vel_ref(P, X, fmaf(X.hx, xr, x0), fmaf(X.hy, yr, y0), fmaf(cs, X.dtT, X.tT), ur, vr);
+        const float un = sg * (f < 2 ? ur : vr) * hn;
+        const float bw = c_rk_b[P.rk][s] * Wq * un;
+        if (un > (float)TIE) {
+          uo += bw;
+          float fx = xr, fy = yr;
+          if (cs != 0.0f) rk_ref(P, X, x0, y0, fx, fy, fmaf(cs, X.dtT, X.tT), -cs * X.dt, -cs * X.dtT);
+          float bx[NN], by[NN];
+          basis_at<NN>(s_xi, s_lam, fx, bx);
+          basis_at<NN>(s_xi, s_lam, fy, by);
+          float val = 0.0f;
+#pragma unroll 1
+          for (int mm = 0; mm < NN; ++mm) {
+            float row = 0.0f;
+#pragma unroll
+            for (int l = 0; l < NN; ++l) row = fmaf(s_psi[mm * NN + l], bx[l], row);
+            val = fmaf(by[mm], row, val);
+          }
+          p1 = fmaf(bw, val, p1);
+          p2 = fmaf(bw * val, val, p2);
+        } else if (un < -(float)TIE) {
+          ui += bw;
+        }
+      }
+      s_face[f][q][0] = uo; s_face[f][q][1] = ui; s_face[f][q][2] = p1; s_face[f][q][3] = p2;
+    }
+    __syncthreads();
+    if (tid < 16) {
+      const int f = tid >> 2, k = tid & 3;
+      float acc = 0.0f;
+      for (int q = 0; q < NN; ++q) acc += s_face[f][q][k];
+      W.faces[(size_t)e * 16 + tid] = acc;
+    }
+  }
+}
+
+template <int NN>
+__global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid_constant__ Mixed2DExtra X,
+                                                     const float* __restrict__ in, Work2M W, float* __restrict__ out,
+                                                     unsigned* status) {
+  constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
+  constexpr int MMAX = 4 * NN + 1;
+  __shared__ float s_xi[NN], s_w[NN], s_l0[NN], s_l1[NN];
+  __shared__ float s_ph[ND], s_a[ND];
+  __shared__ float s_r[MMAX], s_ca[MMAX];
+  __shared__ float s_red[NT / 32];
+  __shared__ float s_scal[4];
+  const int tid = threadIdx.x;
+  const int e = blockIdx.x;
+  const int ex = e % P.kx, ey = e / P.kx;
+  const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
+  const float tn1T = X.tT + X.dtT;
+  if (tid < NN) { s_xi[tid] = X.xi[tid]; s_w[tid] = X.w[tid]; s_l0[tid] = X.l0[tid]; s_l1[tid] = X.l1[tid]; }
+  const bool part = tid < ND;
+  const int i = tid % NN, j = tid / NN;
+  const float ref = W.elem[(size_t)e * 4];
+  float ph = 0.0f;
+  if (part) {
+    ph = W.psihat[(size_t)e * ND + tid];
+    s_ph[tid] = ph;
+  }
+  __syncthreads();
+  const float w2 = part ? s_w[i] * s_w[j] : 0.0f;
+  const bool bnd = (P.cons & SL_C_BOUNDARY) != 0;
+  const int nb_rows = bnd ? 4 * NN : 0;
+  if (bnd && tid < 4 * NN) {
+    const int f = tid / NN, q = tid % NN;
+    const int nb = nb_index(P, ex, ey, f);
+    const float own = W.traces[(size_t)e * 4 * NN + tid];
+    // neighbour's trace relative to this element's reference value
+    const float other = nb >= 0 ? (W.elem[(size_t)nb * 4] - ref) + W.traces[(size_t)nb * 4 * NN + (f ^ 1) * NN + q]
+                                : (float)(P.ghost - (double)ref);
+    const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : s_xi[q];
+    const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : s_xi[q];
+    float ur, vr;
+    vel_ref(P, X, fmaf(X.hx, xr, x0), fmaf(X.hy, yr, y0), tn1T, ur, vr);
+    const float un = (f == 0 || f == 2 ? -1.0f : 1.0f) * (f < 2 ? ur * X.hx : vr * X.hy);
+    float val;
+    if (un > (float)TIE) val = own;
+    else if (un < -(float)TIE) val = other;
+    else val = nb < 0 ? own : 0.5f * (own + other);
+    s_r[tid] = val - own;
+  }
+  const bool mass = (P.cons & SL_C_MASS) != 0, energy = (P.cons & SL_C_ENERGY) != 0;
+  float netm = 0.0f, netd2 = 0.0f, nu = 0.0f;
+  if ((mass || energy) && tid == 0) {
+    // net outflow of mass (increments) and of the squared increments, plus the velocity balance
+    for (int f = 0; f < 4; ++f) {
+      const float* F = W.faces + (size_t)e * 16 + 4 * f;
+      const int nb = nb_index(P, ex, ey, f);
+      nu += F[0] + F[1];
+      netm += F[2];
+      netd2 += F[3];
+      if (nb >= 0) {
+        const float* G = W.faces + (size_t)nb * 16 + 4 * (f ^ 1);
+        const float dref = W.elem[(size_t)nb * 4] - ref;
+        // inflow part: u.n (dref + psi_nb) with the neighbour's u.n = -ours
+        netm += dref * F[1] - G[2];
+        netd2 += dref * dref * F[1] - 2.0f * dref * G[2] - G[3];
+      } else {
+        const float g = (float)(P.ghost - (double)ref);
+        netm += g * F[1];
+        netd2 += g * g * F[1];
+      }
+    }
+    s_scal[0] = netm;
+    s_scal[1] = netd2;
+    s_scal[2] = nu;
+  }
+  __syncthreads();
+  netm = s_scal[0];
+  netd2 = s_scal[1];
+  nu = s_scal[2];
+  const float lam = X.dt_area;               // dt / (hx hy)
+  if (mass) {
+    const float mh = block_sum<NT>(w2 * ph, s_red);
+    // target (increments): sum w psi^n - lam (net increment outflow + ref * closed-surface u.n)
+    if (tid == 0) s_r[nb_rows] = (W.elem[(size_t)e * 4 + 1] - lam * netm - lam * ref * nu) - mh;
+  }
+  __syncthreads();
+  const int m = P.m;
+  float phL = ph;
+  if (part) {
+    float acc = ph;
+    for (int k = 0; k < m; ++k) acc = fmaf(X.Cp[(size_t)tid * m + k], s_r[k], acc);
+    phL = acc;
+  }
+  float cur = phL;
+  bool ok = true;
+  if (energy) {
+    // energy mismatch from increments (mass enforced): -lam ref^2 N_u + sum w (psiL^2 - psi^2) + lam net(delta^2);
+    // without the mass row, add 2 ref times the mass residual
+    const float el2 = block_sum<NT>(w2 * phL * phL, s_red);
+    const float ml = block_sum<NT>(w2 * phL, s_red);
+    const float m1 = W.elem[(size_t)e * 4 + 1], m2 = W.elem[(size_t)e * 4 + 2];
+    float gamma;
+    if (mass) gamma = -lam * ref * ref * nu + (el2 - m2) + lam * netd2;
+    else gamma = fmaf(2.0f * ref, (ml - m1) + lam * netm, lam * ref * ref * nu + (el2 - m2) + lam * netd2);
+    const float escale = block_sum<NT>(part ? w2 * (ref + cur) * (ref + cur) : 0.0f, s_red);
+    float smax = block_max<NT>(part ? fmaxf(fabsf(phL), fabsf(ref)) : 0.0f, s_red);
+    if (smax >= 1e-30f && fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {
+      int exn;
+      frexpf(smax, &exn);
+      const float sc = ldexpf(1.0f, -exn), usc = ldexpf(1.0f, exn);
+      const float rf = ref * sc, gm = gamma * sc * sc;
+      const float ql = phL * sc;
+      float c2 = ql;
+      const float tol = 2.4e-7f * 1.0f + 1e-30f;   // scaled units: values are of order one
+      bool conv = false, feasible = true;
+      for (int it = 0; it < P.picard_cap; ++it) {
+        const float a = w2 * (mass ? c2 : rf + c2);
+        if (part) s_a[tid] = a;
+        __syncthreads();
+        if (bnd && tid < 4 * NN) {
+          const int f = tid / NN, qq = tid % NN;
+          const float* L = (f == 1 || f == 3) ? s_l1 : s_l0;
+          float acc = 0.0f;
+          for (int k = 0; k < NN; ++k) acc = fmaf(f < 2 ? s_a[qq * NN + k] : s_a[k * NN + qq], L[k], acc);
+          s_ca[tid] = acc;
+        }
+        if (mass) {
+          const float cm = block_sum<NT>(w2 * a, s_red);
+          if (tid == 0) s_ca[nb_rows] = cm;
+        }
+        __syncthreads();
+        float q = 0.0f;
+        if (part) {
+          float acc = a;
+          for (int k = 0; k < m; ++k) acc = fmaf(-X.Cp[(size_t)tid * m + k], s_ca[k], acc);
+          q = acc;
+        }
+        float alpha = block_sum<NT>(w2 * ql * q, s_red);
+        if (!mass) alpha = fmaf(rf, block_sum<NT>(w2 * q, s_red), alpha);
+        const float beta = block_sum<NT>(w2 * q * q, s_red);
+        float s;
+        if (beta <= 0.0f) { s = 0.0f; feasible = gm <= 0.0f; }
+        else {
+          const float disc = alpha * alpha - beta * gm;
+          if (disc < 0.0f) { s = -alpha / beta; feasible = false; }
+          else {
+            const float root = sqrtf(disc);
+            const float den = alpha + (alpha >= 0.0f ? root : -root);
+            s = den == 0.0f ? 0.0f : -gm / den;
+            feasible = true;
+          }
+        }
+        const float nv = part ? fmaf(s, q, ql) : 0.0f;
+        const float delta = block_max<NT>(part ? fabsf(nv - c2) : 0.0f, s_red);
+        c2 = nv;
+        if (delta <= tol) { conv = feasible; break; }
+        __syncthreads();
+      }
+      cur = c2 * usc;
+      ok = conv;
+    }
+  }
+  if (part) {
+    const float s = ref + cur;                // TwoSum: hi + lo == ref + cur exactly
+    const float bb = s - ref;
+    const float err = (ref - (s - bb)) + (cur - bb);
+    out[(size_t)e * ND + tid] = s;
+    out[X.plane + (size_t)e * ND + tid] = err;
+    if (!isfinite(s)) atomicOr(status, SL_ST_NONFINITE);
+  }
+  if (!ok && tid == 0) atomicOr(status, SL_ST_PICARD_NOCONV);
+}
+
+template <int NN>
+void launch_n(const StepParams& p, const Mixed2DExtra& x, const float* in, float* out, Work2M w, unsigned* st,
+              cudaStream_t s) {
+  const int nel = p.kx * p.ky;
+  k_p1<NN><<<nel, Shape<NN>::NT, 0, s>>>(p, x, in, w, st);
+  k_p2<NN><<<nel, Shape<NN>::NT, 0, s>>>(p, x, in, w, out, st);
+}
+
+}  // namespace k2m
+}  // namespace sl

@@ -137,8 +137,29 @@ sl_status sl_init(const sl_mesh* mesh, int n, int basis, int precision, void* cu
       c->table_off[mask][soft][2] = put(f.SCt, 1);
     }
   c->red_blocks = 2 * 152;
+  // float copies of the tables for the mixed 2D kernels
+  std::vector<float> ftab;
+  auto fput = [&](const std::vector<double>& v) {
+    size_t off = ftab.size();
+    for (double x : v) ftab.push_back((float)x);
+    ftab.resize(off + std::max<size_t>(v.size(), NMAX), 0.0f);
+    ftab.resize((ftab.size() + 3) & ~size_t(3), 0.0f);
+    return off;
+  };
+  if (mesh->dim == 2 && precision == SL_MIXED) {
+    c->f_off[0] = fput(c->b.xi);
+    c->f_off[1] = fput(c->b.lam);
+    c->f_off[2] = fput(c->b.w);
+    c->f_off[3] = fput(c->b.l0);
+    c->f_off[4] = fput(c->b.l1);
+    for (int mask = 0; mask < 4; ++mask) c->f_cp[mask] = fput(c->fit[mask][0].Cpinv);
+  }
+  const size_t work_bytes = mesh->dim != 2 ? 0
+                            : precision == SL_FP64 ? work2d_doubles(nel, n) * sizeof(double)
+                                                   : work2m_floats(nel, n) * sizeof(float);
   if (cudaMalloc(&c->d_tables, host.size() * sizeof(double)) != cudaSuccess ||
-      (mesh->dim == 2 && cudaMalloc(&c->d_work, work2d_doubles(nel, n) * sizeof(double)) != cudaSuccess) ||
+      (work_bytes && cudaMalloc(&c->d_work, work_bytes) != cudaSuccess) ||
+      (!ftab.empty() && cudaMalloc(&c->d_ftab, ftab.size() * sizeof(float)) != cudaSuccess) ||
       cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc(&c->d_partial, c->red_blocks * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_result, sizeof(double)) != cudaSuccess) {
@@ -147,6 +168,8 @@ sl_status sl_init(const sl_mesh* mesh, int n, int basis, int precision, void* cu
     return fail(nullptr, SL_ENOMEM, "device allocation failed");
   }
   if (cudaMemcpy(c->d_tables, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!ftab.empty() &&
+       cudaMemcpy(c->d_ftab, ftab.data(), ftab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) ||
       cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
     std::string msg = cudaGetErrorString(cudaGetLastError());
     sl_free(c);
@@ -165,6 +188,7 @@ void sl_free(sl_ctx* c) {
   cudaFree(c->d_io);
   cudaFree(c->d_io64);
   cudaFree(c->d_work);
+  cudaFree(c->d_ftab);
   delete c;
 }
 
@@ -244,6 +268,22 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
     Tables1D tb{T + c->off_xi, T + c->off_w, T + c->off_lam, T + c->off_l0, T + c->off_l1,
                 T + off[0], T + off[1], T + off[2]};
     launch_step2d_f64(c->n, P, tb, (const double*)phi_in, (double*)phi_out, c->d_work, c->d_status, c->stream);
+  } else if (M.dim == 2 && c->precision == SL_MIXED) {
+    if (opt->bvalue != SL_BV_INTERP)
+      return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
+    if (opt->fit != SL_FIT_HARD) return fail(c, SL_EUNSUPPORTED, "the 2D mixed path uses the hard fit");
+    const float* F = c->d_ftab;
+    Mixed2DExtra X{F + c->f_off[0], F + c->f_off[1], F + c->f_off[2], F + c->f_off[3], F + c->f_off[4],
+                   F + c->f_cp[lin], plane_stride(c->nvals),
+                   (float)hx, (float)hy, (float)(1.0 / hx), (float)(1.0 / hy),
+                   (float)vel->p[0], (float)vel->p[1], (float)vel->p[0], (float)vel->p[1], (float)vel->p[2],
+                   0.0f, 0.0f, (float)dt, (float)(dt / (hx * hy))};
+    if (vel->kind == SL_VEL_SWIRL) {
+      X.tT = (float)(t / vel->p[0]);
+      X.dtT = (float)(dt / vel->p[0]);
+    }
+    launch_step2d_mixed(c->n, P, X, (const float*)phi_in, (float*)phi_out, (float*)c->d_work, c->d_status,
+                        c->stream);
   } else {
     return fail(c, SL_EUNSUPPORTED, "this dimension/precision combination is not built yet");
   }

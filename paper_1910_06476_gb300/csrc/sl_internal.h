@@ -84,6 +84,24 @@ void launch_step2d_f64(int n, const StepParams& p, const Tables1D& tb, const dou
                        unsigned* status, cudaStream_t s);
 inline int64_t work2d_doubles(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 8); }
 
+// Extra parameters of the 2D mixed-precision kernels (float tables and scalars), by value
+struct Mixed2DExtra {
+  const float* xi;
+  const float* lam;
+  const float* w;
+  const float* l0;
+  const float* l1;
+  const float* Cp;                       // [n^2][m] pseudo-inverse of the active rows (hard fit)
+  int64_t plane;                         // float offset of the lo plane
+  float hx, hy, ihx, ihy;
+  float a, b, om, cx, cy;                // velocity parameters (constant / rotation)
+  float tT, dtT;                         // t / T and dt / T (swirl)
+  float dt, dt_area;                     // dt and dt / (hx hy)
+};
+void launch_step2d_mixed(int n, const StepParams& p, const Mixed2DExtra& x, const float* in, float* out, float* work,
+                         unsigned* status, cudaStream_t s);
+inline int64_t work2m_floats(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 16 + 4); }
+
 // Kernel parameter block of the 1D shared-operator (mixed precision) step; passed by value.
 struct Mixed1DParams {
   int n, K, left_up, periodic, m, mass_on, energy_on, nst;
@@ -138,6 +156,9 @@ struct sl_ctx {
   void* d_io = nullptr;                  // device buffers for sl_run_host
   double* d_io64 = nullptr;
   double* d_work = nullptr;              // 2D workspace between the two phases
+  float* d_ftab = nullptr;               // float tables of the mixed 2D path
+  size_t f_off[5] = {};                  // xi, lam, w, l0, l1
+  size_t f_cp[4] = {};                   // float pseudo-inverse per linear-row mask
   // cached shared operator of the mixed 1D path, keyed on (a, dt, constraints, rk, fit)
   bool mix_valid = false;
   double mix_a = 0, mix_dt = 0;

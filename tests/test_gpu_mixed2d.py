@@ -1,0 +1,143 @@
+"""GPU parity of the mixed-precision 2D path (double-float state, float arithmetic on
+per-element increments) against the FP64 oracle and the FP64 GPU path.
+
+Bound: relative L2 <= 1e-6 against FP64 after 1 step and after 1000 steps (500 for the
+constant-velocity problem, its configured run length)."""
+import numpy as np
+import pytest
+
+import sl_inputs
+from oracle import sl_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def sl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_06476_gb300 import build as B
+    B.build()
+    import paper_1910_06476_gb300 as pkg
+    return pkg
+
+
+def rel(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+CASES = [
+    # kx, ky, n, kind, params, bc, cons, rk, data
+    (6, 5, 9, 0, (1.0, 0.5), 0, 3, 4, "sincos"),
+    (4, 4, 5, 0, (-0.8, 0.6), 0, 7, 4, "sincos"),
+    (5, 4, 6, 0, (1.0, 0.5), 0, 1, 2, "sincos"),
+    (1, 1, 7, 0, (1.0, 0.5), 0, 3, 4, "sincos"),
+    (6, 6, 6, 1, (2 * np.pi, 0.5, 0.5), 1, 3, 4, "hill"),
+    (5, 5, 8, 2, (5.0,), 1, 7, 4, "bell"),
+    (5, 5, 8, 2, (5.0,), 1, 7, 4, "sincos"),
+    (3, 3, 12, 1, (2 * np.pi, 0.5, 0.5), 1, 3, 3, "sincos"),
+    (2, 2, 16, 0, (0.6, 0.9), 0, 3, 4, "sincos"),
+]
+
+DATA = {"sincos": lambda x, y: 1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y),
+        "hill": sl_inputs.hill_2d, "bell": sl_inputs.cosine_bell_2d}
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}n{c[2]}v{c[3]}c{c[6]}{c[8]}" for c in CASES])
+def test_mixed2d_step_parity(sl, case):
+    kx, ky, n, kind, p, bc, cons, rk, data = case
+    box = (0.0, 1.0, 0.0, 1.0)
+    ctx = sl.Context(2, kx, ky, box, n, 0, sl.MIXED, (bc,) * 4, 0.1 if bc else 0.0)
+    setup = O.Setup(2, kx, ky, box, n, 0, (bc,) * 4, 0.1 if bc else 0.0)
+    gv = sl.velocity(kind, *p)
+    ov = O.Vel(kind, tuple(p) + (0,) * (6 - len(p)))
+    x, y = ctx.node_coords()
+    phi = DATA[data](x, y) + 0.02 * sl_inputs.random_state(x.shape, kx + n)
+    dt = ctx.max_dt(gv)
+    a = ctx.pack(torch.tensor(phi.ravel(), device="cuda"))
+    b = ctx.new_state()
+    ctx.step(a, b, gv, 0.3, dt, sl.options(cons, rk))
+    bits = ctx.sync()
+    got = ctx.unpack(b).cpu().numpy().reshape(ky, kx, n, n)
+    ref, infos = O.step_2d(setup, phi, O.StepOpts(ov, 0.3, dt, cons, rk))
+    conv = np.array([[infos[(ex, ey)]["converged"] for ex in range(kx)] for ey in range(ky)])
+    assert conv.all()
+    assert bits == 0, bits
+    assert rel(got, ref) <= TOL
+
+
+def _long_run(sl, prob, n, steps, kind, p):
+    c64 = sl.Context(2, prob.kx, prob.ky, prob.box, n, 0, sl.FP64, prob.bc, prob.ghost)
+    cm = sl.Context(2, prob.kx, prob.ky, prob.box, n, 0, sl.MIXED, prob.bc, prob.ghost)
+    gv = sl.velocity(kind, *p)
+    dt = c64.max_dt(gv)
+    x, y = c64.node_coords()
+    phi = torch.tensor(prob.phi0(x, y).ravel(), device="cuda")
+    a64, b64 = phi.clone(), torch.empty_like(phi)
+    am, bm = cm.pack(phi), cm.new_state()
+    opts = sl.options(prob.constraints, 4)
+    errs = {}
+    m0 = c64.mass(a64)
+    for s in range(steps):
+        c64.step(a64, b64, gv, s * dt, dt, opts)
+        cm.step(am, bm, gv, s * dt, dt, opts)
+        a64, b64 = b64, a64
+        am, bm = bm, am
+        if s + 1 in (1, steps):
+            d = cm.unpack(am) - a64
+            errs[s + 1] = (d.norm() / a64.norm()).item()
+    return c64, cm, a64, am, errs, m0
+
+
+def test_mixed2d_config3_shape_500_steps(sl):
+    """Config 3's problem (velocity (1, 0.5), sin cos data, boundary + mass) at 16 x 16, n = 9."""
+    prob = sl_inputs.config3_2d_const(n=9, k=16)
+    c64, cm, a64, am, errs, m0 = _long_run(sl, prob, 9, 500, sl.VEL_CONST, (1.0, 0.5))
+    assert c64.sync() == 0 and cm.sync() == 0
+    assert errs[1] <= TOL and errs[500] <= TOL, errs
+    assert abs(cm.mass(am) - m0) <= 1e-9
+
+
+def test_mixed2d_swirl_1000_steps(sl):
+    """Config 5's problem (swirl, cosine bell, boundary + mass + energy) at 24 x 24, n = 8."""
+    prob = sl_inputs.config5_swirl(n=8, k=24)
+    c64, cm, a64, am, errs, m0 = _long_run(sl, prob, 8, 1000, sl.VEL_SWIRL, (5.0,))
+    assert c64.sync() == 0 and cm.sync() == 0
+    assert errs[1] <= TOL and errs[1000] <= TOL, errs
+
+
+def test_mixed2d_swirl_1024_sampled(sl):
+    """Swirl at 1024 x 1024 elements, n = 8: sampled elements recomputed by the oracle from the
+    GPU state before the step."""
+    prob = sl_inputs.config5_swirl(n=8, k=1024)
+    K = prob.kx
+    cm = sl.Context(2, K, K, prob.box, 8, 0, sl.MIXED, prob.bc, prob.ghost)
+    setup = O.setup_from_problem(prob)
+    gv = sl.velocity(sl.VEL_SWIRL, 5.0)
+    dt = cm.max_dt(gv)
+    x, y = cm.node_coords()
+    am = cm.pack(torch.tensor(prob.phi0(x, y).ravel(), device="cuda"))
+    del x, y
+    bm = cm.new_state()
+    opts = sl.options(prob.constraints, 4)
+    for s in range(3):
+        cm.step(am, bm, gv, s * dt, dt, opts)
+        am, bm = bm, am
+    pre = cm.unpack(am).cpu().numpy().reshape(K, K, 8, 8)
+    cm.step(am, bm, gv, 3 * dt, dt, opts)
+    assert cm.sync() == 0
+    got = cm.unpack(bm).cpu().numpy().reshape(K, K, 8, 8)
+    # elements on the bell (centre (0.5, 0.75), radius 0.15) plus a random sample
+    cx, cy = int(0.5 * K), int(0.75 * K)
+    elems = [(cx + dx, cy + dy) for dx in (-100, -60, 0, 40, 120) for dy in (-120, -30, 0, 50, 140)]
+    idx = sl_inputs.sample_elements(20, K * K, 4)
+    elems += [(int(e % K), int(e // K)) for e in idx]
+    ref, _ = O.step_2d(setup, pre, O.StepOpts(O.Vel(O.VEL_SWIRL, (5.0, 0, 0, 0, 0, 0)), 3 * dt, dt,
+                                              prob.constraints, 4), elements=elems)
+    g = np.stack([got[ey, ex] for ex, ey in elems])
+    r = np.stack([ref[ey, ex] for ex, ey in elems])
+    assert rel(g, r) <= TOL
