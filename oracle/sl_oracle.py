@@ -38,7 +38,10 @@ in the design notes):
       The energy row is applied only when the linear fit misses the energy target by more
       than 1e-12 relative: on nearly constant data the row is almost a multiple of the mass
       row, its direction is set by a variation near rounding level, and a correction would
-      only amplify rounding noise.
+      only amplify rounding noise.  Where the iteration does not converge within its cap (or
+      ends on an unreachable target), the element keeps the linear-constraint solution and
+      reports it: the paper finds the energy-constrained cases unstable, and a non-converged
+      iterate has no unique value.
   R8  Upwinding by the sign of u.n at the face point (at t^{n+1} for boundary values, at the
       stage time for fluxes); |u.n| <= TIE is a tie: interior faces average both traces,
       non-periodic domain faces keep their own trace.
@@ -373,14 +376,15 @@ def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode
             delta = float(np.max(np.abs(new - phi)))
             phi = new
             if delta < tol:
-                return phi, it, feasible
-        return phi, cap, False
+                return (phi, it, True) if feasible else (phiL, it, False)
+        return phiL, cap, False                    # not converged: keep the linear fit
     phi = fit_soft(phihat, C_lin, d_lin)
     if energy_row_weights is None:
         return phi, 0, True
     EL = float(np.dot(energy_row_weights, phi * phi))
     if abs(EL - E_target) <= ENERGY_SKIP_RTOL * max(abs(E_target), EL):
         return phi, 0, True
+    phiL = phi
     for it in range(1, cap + 1):
         a = energy_row_weights * phi
         new = fit_soft(phihat, np.vstack([C_lin, a[None, :]]), np.concatenate([d_lin, [E_target]]))
@@ -388,7 +392,7 @@ def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode
         phi = new
         if delta < tol:
             return phi, it, True
-    return phi, cap, False
+    return phiL, cap, False                        # not converged: keep the linear fit
 
 
 # ============================================================================ 1D step

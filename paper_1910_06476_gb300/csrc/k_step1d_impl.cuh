@@ -387,7 +387,11 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
         if (delta < tol) { conv = true; break; }
       }
     }
-    if (!conv) ok = false;
+    if (!conv) {                          // keep the linear-constraint solution
+      ok = false;
+#pragma unroll
+      for (int i = 0; i < NN; ++i) res_phi[i] = phL[i];
+    }
   }
   bool finite = true;
 #pragma unroll

@@ -204,8 +204,10 @@ __global__ void __launch_bounds__(TILE) k_step1d_mixed(const __grid_constant__ M
             }
             if (delta <= tol) { conv = feasible; break; }
           }
+          if (conv) {
 #pragma unroll
-          for (int i = 0; i < NN; ++i) res[i] = cur[i] * usc;
+            for (int i = 0; i < NN; ++i) res[i] = cur[i] * usc;
+          }                                   // else: keep the linear-constraint solution
           ok = conv;
         }
       }

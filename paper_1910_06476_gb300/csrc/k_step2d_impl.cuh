@@ -487,6 +487,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, Tables1D tb,
         __syncthreads();
       }
       ok = conv;
+      if (!conv) cur = phL;                   // keep the linear-constraint solution
     }
   }
   if (part) {

@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
         if (delta <= tol) { conv = feasible; break; }
         __syncthreads();
       }
-      cur = c2 * usc;
+      if (conv) cur = c2 * usc;               // else keep the linear-constraint solution
       ok = conv;
     }
   }
