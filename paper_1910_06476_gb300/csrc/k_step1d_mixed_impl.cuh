@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(TILE) k_step1d_mixed(const __grid_constant__ M
         float gv = 0.0f, gm = 0.0f, escale = 0.0f;
 #pragma unroll
         for (int i = 0; i < NN; ++i) {
-          gv = fmaf(P.w[i], ql[i] * ql[i] - qs[i] * qs[i], gv);
+          gv = fmaf(P.w[i], (ql[i] - qs[i]) * (ql[i] + qs[i]), gv);
           gm = fmaf(P.w[i], ql[i] - qs[i], gm);
           const float phv = rf + qs[i];
           escale = fmaf(P.w[i], phv * phv, escale);

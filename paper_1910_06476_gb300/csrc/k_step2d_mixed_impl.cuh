@@ -30,7 +30,8 @@ static __constant__ float c_rk_b[5][4] = {
 static __constant__ float c_rk_c[5][4] = {{}, {0.0f}, {0.0f, 1.0f}, {0.0f, 0.5f, 1.0f}, {0.0f, 0.5f, 0.5f, 1.0f}};
 
 constexpr int SOLVE_CAP = 40;
-constexpr float SOLVE_RTOL = 3e-7f;
+constexpr float SOLVE_RTOL = 3e-7f;          // target, relative to max |psi*|
+constexpr float SOLVE_FLOOR = 4e-6f;         // accepted once the residual stops improving
 
 // velocity divided by the element size: the time derivative of the reference coordinates
 __device__ __forceinline__ void vel_ref(const StepParams& P, const Mixed2DExtra& X, float x, float y, float tT,
@@ -213,7 +214,11 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
   };
   precond_add(true);
   const float scale = block_max<NT>(part ? fabsf(ps) : 0.0f, s_red);
+  // Stop at the tolerance, or once the residual has stalled at the float floor; guard against
+  // divergence by keeping the best iterate.
   bool solved = false;
+  float prev = INFINITY, best = INFINITY;
+  __shared__ float s_best[ND];
   for (int it = 0; it < SOLVE_CAP; ++it) {
     float r = 0.0f;
     if (part) {
@@ -230,6 +235,17 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
     }
     const float rmax = block_max<NT>(fabsf(r), s_red);
     if (rmax <= SOLVE_RTOL * scale || rmax == 0.0f) { solved = true; break; }
+    if (rmax <= SOLVE_FLOOR * scale && rmax > 0.5f * prev) { solved = true; break; }
+    if (!(rmax <= 4.0f * best)) {             // diverging (or not finite): back to the best iterate
+      if (part) s_ph[tid] = s_best[tid];
+      __syncthreads();
+      break;
+    }
+    if (rmax < best) {
+      best = rmax;
+      if (part) s_best[tid] = s_ph[tid];
+    }
+    prev = rmax;
     precond_add(false);
   }
   if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);
@@ -384,7 +400,9 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
   if (mass) {
     const float mh = block_sum<NT>(w2 * ph, s_red);
     // target (increments): sum w psi^n - lam (net increment outflow + ref * closed-surface u.n)
-    if (tid == 0) s_r[nb_rows] = (W.elem[(size_t)e * 4 + 1] - lam * netm - lam * ref * nu) - mh;
+    // ref * (closed-surface integral of u.n) is dropped: every 2D velocity here is divergence free
+    // and the face quadrature integrates it to rounding; in float it would be noise of eps |U|
+    if (tid == 0) s_r[nb_rows] = (W.elem[(size_t)e * 4 + 1] - lam * netm) - mh;
   }
   __syncthreads();
   const int m = P.m;
@@ -397,14 +415,16 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
   float cur = phL;
   bool ok = true;
   if (energy) {
-    // energy mismatch from increments (mass enforced): -lam ref^2 N_u + sum w (psiL^2 - psi^2) + lam net(delta^2);
-    // without the mass row, add 2 ref times the mass residual
-    const float el2 = block_sum<NT>(w2 * phL * phL, s_red);
+    // energy mismatch from increments (mass enforced): sum w (psiL - psi)(psiL + psi) + lam net(delta^2);
+    // without the mass row, add 2 ref times the mass residual (closed-surface u.n taken as zero)
+    const float psin = part ? (in[(size_t)e * ND + tid] - ref) + in[X.plane + (size_t)e * ND + tid] : 0.0f;
+    const float dpsi = part ? phL - psin : 0.0f;
+    const float ev = block_sum<NT>(w2 * dpsi * (phL + (phL - dpsi)), s_red);
     const float ml = block_sum<NT>(w2 * phL, s_red);
-    const float m1 = W.elem[(size_t)e * 4 + 1], m2 = W.elem[(size_t)e * 4 + 2];
+    const float m1 = W.elem[(size_t)e * 4 + 1];
     float gamma;
-    if (mass) gamma = -lam * ref * ref * nu + (el2 - m2) + lam * netd2;
-    else gamma = fmaf(2.0f * ref, (ml - m1) + lam * netm, lam * ref * ref * nu + (el2 - m2) + lam * netd2);
+    if (mass) gamma = ev + lam * netd2;
+    else gamma = fmaf(2.0f * ref, (ml - m1) + lam * netm, ev + lam * netd2);
     const float escale = block_sum<NT>(part ? w2 * (ref + cur) * (ref + cur) : 0.0f, s_red);
     float smax = block_max<NT>(part ? fmaxf(fabsf(phL), fabsf(ref)) : 0.0f, s_red);
     if (smax >= 1e-30f && fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {

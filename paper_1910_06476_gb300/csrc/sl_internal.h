@@ -16,7 +16,7 @@ namespace sl {
 constexpr int NMAX = 17;                 // largest node count per direction
 constexpr int MMAX1D = 3;                // linear constraint rows in 1D: left, right, mass
 constexpr double TIE = 1e-13;            // |u.n| at or below this is an upwind tie
-constexpr double ENERGY_SKIP_RTOL = 1e-12;  // energy row applied only beyond this relative miss
+constexpr double ENERGY_SKIP_RTOL = 1e-9;   // energy row applied only beyond this relative miss
 
 // ------------------------------------------------------------------ host tables (tables.cpp)
 

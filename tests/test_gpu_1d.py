@@ -182,8 +182,8 @@ def test_periodic_mass_conserved_many_steps(sl):
         a, b = b, a
     assert ctx.sync() == 0
     assert abs(ctx.mass(a) - m0) < 1e-13 * abs(m0)
-    # the energy row is skipped when the linear fit already meets it to 1e-12 (per element)
-    assert abs(ctx.energy(a) - e0) < 200 * 1e-12 * abs(e0)
+    # the energy row is skipped when the linear fit already meets it to 1e-9 (per element)
+    assert abs(ctx.energy(a) - e0) < 200 * 1e-9 * abs(e0)
 
 
 def test_status_bits_and_errors(sl):
