@@ -55,6 +55,7 @@ class Problem:
     t0: float = 0.0
     phi0: object = None     # callable phi0(x[, y]) -> array (plain numpy)
     orders: object = None   # optional per-element node counts (p-adaptive), shape (ky, kx)
+    dt_rule: str = "paper"  # "paper": edge-node gap, factor 1; "half_min_spacing": half the min spacing
     extra: dict = field(default_factory=dict)
 
 
@@ -103,7 +104,7 @@ def config1_1d_sine(n=9, k=16):
     """1D periodic [0,1], u = 1, sin(2 pi x), K=16, 9 Gauss-Legendre nodes, boundary only, RK4, FP64."""
     return Problem("1d_sine_K16_n9", 1, k, 1, (0.0, 1.0, 0.0, 0.0), n, GAUSS_LEGENDRE,
                    Velocity(VEL_CONST, (1.0, 0, 0, 0, 0, 0)), (BC_PERIODIC,) * 4, 0.0,
-                   C_BOUNDARY, 4, phi0=sine_1d)
+                   C_BOUNDARY, 4, phi0=sine_1d, dt_rule="half_min_spacing")
 
 
 def config2_1d_gauss(n=9, k=1 << 20):
@@ -171,6 +172,11 @@ def sample_elements(count, total, seed):
     rng = np.random.default_rng(seed)
     count = min(count, total)
     return np.sort(rng.choice(total, size=count, replace=False))
+
+
+def rule_code(prob):
+    """Time-step rule of a problem as the C ABI enumeration (0: half min spacing, 1: paper)."""
+    return 1 if prob.dt_rule == "paper" else 0
 
 
 def steps_to(T, dt0):

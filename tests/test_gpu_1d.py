@@ -137,7 +137,7 @@ def test_full_size_sampled_parity(sl):
     prob = sl_inputs.config2_1d_gauss(9)
     ctx, setup = make(sl, prob.kx, prob.n)
     gv = sl.velocity(sl.VEL_CONST, 1.0)
-    dt = ctx.max_dt(gv)
+    dt = ctx.max_dt(gv, sl_inputs.rule_code(prob))
     x, _ = ctx.node_coords()
     a = torch.tensor(prob.phi0(x), device="cuda")
     b = torch.empty_like(a)

@@ -106,7 +106,7 @@ def test_2d_multistep_parity_and_mass(sl):
     ctx = sl.Context(2, 4, 4, prob.box, 7, 0, sl.FP64, prob.bc, 0.0)
     setup = O.setup_from_problem(prob)
     gv = sl.velocity(sl.VEL_CONST, 1.0, 0.5)
-    dt = ctx.max_dt(gv)
+    dt = ctx.max_dt(gv, sl_inputs.rule_code(prob))
     x, y = ctx.node_coords()
     a = torch.tensor(prob.phi0(x, y).ravel(), device="cuda")
     b = torch.empty_like(a)

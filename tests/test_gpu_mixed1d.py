@@ -87,7 +87,7 @@ def test_mixed_1000_steps_vs_fp64(sl, n, cons):
     c64 = sl.Context(1, K, 1, prob.box, n, 0, sl.FP64, prob.bc, prob.ghost)
     cm = mixed_ctx(sl, K, n)
     gv = sl.velocity(sl.VEL_CONST, 1.0)
-    dt = c64.max_dt(gv)
+    dt = c64.max_dt(gv, sl_inputs.rule_code(prob))
     x, _ = c64.node_coords()
     phi = torch.tensor(prob.phi0(x).ravel(), device="cuda")
     a64, b64 = phi.clone(), torch.empty_like(phi)
@@ -115,7 +115,7 @@ def test_mixed_full_size_sampled(sl):
     cm = mixed_ctx(sl, prob.kx, 9)
     setup = O.setup_from_problem(prob)
     gv = sl.velocity(sl.VEL_CONST, 1.0)
-    dt = cm.max_dt(gv)
+    dt = cm.max_dt(gv, sl_inputs.rule_code(prob))
     x, _ = cm.node_coords()
     am = cm.pack(torch.tensor(prob.phi0(x).ravel(), device="cuda"))
     bm = cm.new_state()

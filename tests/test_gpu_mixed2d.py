@@ -74,7 +74,7 @@ def _long_run(sl, prob, n, steps, kind, p):
     c64 = sl.Context(2, prob.kx, prob.ky, prob.box, n, 0, sl.FP64, prob.bc, prob.ghost)
     cm = sl.Context(2, prob.kx, prob.ky, prob.box, n, 0, sl.MIXED, prob.bc, prob.ghost)
     gv = sl.velocity(kind, *p)
-    dt = c64.max_dt(gv)
+    dt = c64.max_dt(gv, sl_inputs.rule_code(prob))
     x, y = c64.node_coords()
     phi = torch.tensor(prob.phi0(x, y).ravel(), device="cuda")
     a64, b64 = phi.clone(), torch.empty_like(phi)
@@ -106,9 +106,8 @@ def test_mixed2d_config3_500_steps(sl):
 
 
 def test_mixed2d_swirl_1000_steps(sl):
-    """Config 5's problem (swirl, cosine bell, boundary + mass + energy) at 128 x 128, n = 8 (the
-    bell spans 19 elements in radius; at 24 x 24, 3.6 elements, the float path grows unstable
-    at the unresolved bell edge after a few hundred steps while FP64 does not)."""
+    """Config 5's problem (swirl, cosine bell, boundary + mass + energy) at 128 x 128, n = 8, with
+    the paper's time step (particles stay inside their elements)."""
     prob = sl_inputs.config5_swirl(n=8, k=128)
     c64, cm, a64, am, errs, m0 = _long_run(sl, prob, 8, 1000, sl.VEL_SWIRL, (5.0,))
     # the energy iteration does not converge at some elements of the bell's edge (both paths);
@@ -125,7 +124,7 @@ def test_mixed2d_swirl_1024_sampled(sl):
     cm = sl.Context(2, K, K, prob.box, 8, 0, sl.MIXED, prob.bc, prob.ghost)
     setup = O.setup_from_problem(prob)
     gv = sl.velocity(sl.VEL_SWIRL, 5.0)
-    dt = cm.max_dt(gv)
+    dt = cm.max_dt(gv, sl_inputs.rule_code(prob))
     x, y = cm.node_coords()
     am = cm.pack(torch.tensor(prob.phi0(x, y).ravel(), device="cuda"))
     del x, y
