@@ -31,7 +31,8 @@ static __constant__ float c_rk_c[5][4] = {{}, {0.0f}, {0.0f, 1.0f}, {0.0f, 0.5f,
 
 constexpr int SOLVE_CAP = 40;
 constexpr float SOLVE_RTOL = 3e-7f;          // target, relative to max |psi*|
-constexpr float SOLVE_FLOOR = 4e-6f;         // accepted once the residual stops improving
+constexpr float SOLVE_STALL = 4e-6f;         // a residual that stops improving below this is the float floor
+constexpr float SOLVE_FLOOR = 1e-4f;         // best residual accepted when the iteration stalls or diverges
 
 // velocity divided by the element size: the time derivative of the reference coordinates
 __device__ __forceinline__ void vel_ref(const StepParams& P, const Mixed2DExtra& X, float x, float y, float tT,
@@ -54,22 +55,24 @@ __device__ __forceinline__ void vel_ref(const StepParams& P, const Mixed2DExtra&
   }
 }
 
-// one RK step of the reference coordinates (xi, eta) of a point of the element with origin
-// (x0, y0); tT = t / T (swirl), h = step in time, hT = h / T
-__device__ __forceinline__ void rk_ref(const StepParams& P, const Mixed2DExtra& X, float x0, float y0, float& xi,
-                                       float& eta, float tT, float h, float hT) {
+// One RK step of the displacement (dx, dy), in reference coordinates, of the point (bx, by) of
+// the element with origin (x0, y0); tT = t / T (swirl), h = step in time, hT = h / T.  The
+// displacement is integrated by itself (not the position), so that its float rounding is
+// relative to the displacement and not to the coordinate.
+__device__ __forceinline__ void rk_disp(const StepParams& P, const Mixed2DExtra& X, float x0, float y0, float bx,
+                                        float by, float& dx, float& dy, float tT, float h, float hT) {
   const int S = c_rk_s[P.rk];
   float kx[4], ky[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     if (s < S) {
-      float xs = xi, ys = eta;
+      float xs = dx, ys = dy;
 #pragma unroll
       for (int j = 0; j < s; ++j) {
         xs = fmaf(h * c_rk_a[P.rk][s][j], kx[j], xs);
         ys = fmaf(h * c_rk_a[P.rk][s][j], ky[j], ys);
       }
-      vel_ref(P, X, fmaf(X.hx, xs, x0), fmaf(X.hy, ys, y0), fmaf(c_rk_c[P.rk][s], hT, tT), kx[s], ky[s]);
+      vel_ref(P, X, fmaf(X.hx, bx + xs, x0), fmaf(X.hy, by + ys, y0), fmaf(c_rk_c[P.rk][s], hT, tT), kx[s], ky[s]);
     }
   }
   float sx = 0.0f, sy = 0.0f;
@@ -79,15 +82,17 @@ __device__ __forceinline__ void rk_ref(const StepParams& P, const Mixed2DExtra& 
       sx = fmaf(c_rk_b[P.rk][s], kx[s], sx);
       sy = fmaf(c_rk_b[P.rk][s], ky[s], sy);
     }
-  xi = fmaf(h, sx, xi);
-  eta = fmaf(h, sy, eta);
+  dx = fmaf(h, sx, dx);
+  dy = fmaf(h, sy, dy);
 }
 
+// Lagrange basis at z = z0 + dz with the differences formed as (z0 - xi_k) + dz: when z0 is a
+// node, its own difference is dz exactly
 template <int NN>
-__device__ __forceinline__ void basis_at(const float* xi, const float* lam, float z, float* out) {
+__device__ __forceinline__ void basis_at(const float* xi, const float* lam, float z0, float dz, float* out) {
   float d[NN], pre[NN];
 #pragma unroll
-  for (int k = 0; k < NN; ++k) d[k] = z - xi[k];
+  for (int k = 0; k < NN; ++k) d[k] = (z0 - xi[k]) + dz;
   float acc = 1.0f;
 #pragma unroll
   for (int k = 0; k < NN; ++k) { pre[k] = acc; acc *= d[k]; }
@@ -177,21 +182,21 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
   // advect the particle of node (i, j) in reference coordinates
   float Lx[NN], Ly[NN], ps = 0.0f, dxs = 0.0f, dys = 0.0f;
   if (part) {
-    float xs = s_xi[i], ys = s_xi[j];
-    rk_ref(P, X, x0, y0, xs, ys, X.tT, X.dt, X.dtT);
-    basis_at<NN>(s_xi, s_lam, xs, Lx);
-    basis_at<NN>(s_xi, s_lam, ys, Ly);
+    float ddx = 0.0f, ddy = 0.0f;
+    rk_disp(P, X, x0, y0, s_xi[i], s_xi[j], ddx, ddy, X.tT, X.dt, X.dtT);
+    basis_at<NN>(s_xi, s_lam, s_xi[i], ddx, Lx);
+    basis_at<NN>(s_xi, s_lam, s_xi[j], ddy, Ly);
     ps = s_psi[tid];
-    dxs = xs - s_xi[i];
-    dys = ys - s_xi[j];
+    dxs = ddx;
+    dys = ddy;
   }
   const float mdx = block_sum<NT>(dxs, s_red) / ND;
   const float mdy = block_sum<NT>(dys, s_red) / ND;
   if (part) {
     float b[NN];
-    basis_at<NN>(s_xi, s_lam, s_xi[j] - mdx, b);
+    basis_at<NN>(s_xi, s_lam, s_xi[j], -mdx, b);
     s_Rx[tid] = b[i];
-    basis_at<NN>(s_xi, s_lam, s_xi[j] - mdy, b);
+    basis_at<NN>(s_xi, s_lam, s_xi[j], -mdy, b);
     s_Ry[tid] = b[i];
     s_r[tid] = ps;
   }
@@ -234,11 +239,16 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
       s_r[tid] = r;
     }
     const float rmax = block_max<NT>(fabsf(r), s_red);
-    if (rmax <= SOLVE_RTOL * scale || rmax == 0.0f) { solved = true; break; }
-    if (rmax <= SOLVE_FLOOR * scale && rmax > 0.5f * prev) { solved = true; break; }
-    if (!(rmax <= 4.0f * best)) {             // diverging (or not finite): back to the best iterate
-      if (part) s_ph[tid] = s_best[tid];
-      __syncthreads();
+    // values below the normal float range carry no accuracy to refine
+    if (rmax <= SOLVE_RTOL * scale || rmax == 0.0f || scale < 1e-30f) { solved = true; break; }
+    const bool stalled = rmax > 0.5f * prev && rmax <= SOLVE_STALL * scale;   // at the float floor
+    const bool diverging = !(rmax <= 4.0f * best);                             // or not finite
+    if (stalled || diverging) {
+      if (!(rmax <= best)) {                  // back to the best iterate
+        if (part) s_ph[tid] = s_best[tid];
+        __syncthreads();
+      }
+      solved = fminf(rmax, best) <= SOLVE_FLOOR * scale;
       break;
     }
     if (rmax < best) {
@@ -288,11 +298,11 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
         const float bw = c_rk_b[P.rk][s] * Wq * un;
         if (un > (float)TIE) {
           uo += bw;
-          float fx = xr, fy = yr;
-          if (cs != 0.0f) rk_ref(P, X, x0, y0, fx, fy, fmaf(cs, X.dtT, X.tT), -cs * X.dt, -cs * X.dtT);
+          float fdx = 0.0f, fdy = 0.0f;
+          if (cs != 0.0f) rk_disp(P, X, x0, y0, xr, yr, fdx, fdy, fmaf(cs, X.dtT, X.tT), -cs * X.dt, -cs * X.dtT);
           float bx[NN], by[NN];
-          basis_at<NN>(s_xi, s_lam, fx, bx);
-          basis_at<NN>(s_xi, s_lam, fy, by);
+          basis_at<NN>(s_xi, s_lam, xr, fdx, bx);
+          basis_at<NN>(s_xi, s_lam, yr, fdy, by);
           float val = 0.0f;
 #pragma unroll 1
           for (int mm = 0; mm < NN; ++mm) {
