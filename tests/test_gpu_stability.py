@@ -42,3 +42,28 @@ def run_max(sl, kind, p, data, rule, steps, cons=3):
 def test_paper_time_step_is_stable_half_spacing_is_not(sl, kind, p, data):
     assert run_max(sl, kind, p, data, sl.RULE_PAPER, 600) <= 1.01
     assert not run_max(sl, kind, p, data, sl.RULE_HALF_MIN_SPACING, 600) <= 10.0
+
+
+def test_swirl_transient_amplification_fp64(sl):
+    """Measured property of the discrete scheme on the swirl flow (config 5's problem, 512 x 512,
+    n = 8, boundary + mass, paper's time step): a 1e-12 perturbation of the FP64 state grows by more
+    than six orders of magnitude within 1000 steps, while the solution stays bounded.  This is
+    why long mixed-versus-FP64 comparisons on this flow are limited to short horizons."""
+    prob = sl_inputs.config5_swirl(n=8, k=512)
+    c = sl.Context(2, 512, 512, prob.box, 8, 0, sl.FP64, prob.bc, prob.ghost)
+    gv = sl.velocity(sl.VEL_SWIRL, 5.0)
+    dt = c.max_dt(gv, sl.RULE_PAPER)
+    x, y = c.node_coords()
+    phi = torch.tensor(prob.phi0(x, y).ravel(), device="cuda")
+    pert = torch.tensor(sl_inputs.random_state(phi.shape, 5), device="cuda") * 1e-12 * (phi != 0)
+    a1, b1 = phi.clone(), torch.empty_like(phi)
+    a2, b2 = phi + pert, torch.empty_like(phi)
+    for s in range(1000):
+        c.step(a1, b1, gv, s * dt, dt, sl.options(3, 4))
+        c.step(a2, b2, gv, s * dt, dt, sl.options(3, 4))
+        a1, b1 = b1, a1
+        a2, b2 = b2, a2
+    c.sync()
+    growth = (a2 - a1).abs().max().item() / 1e-12
+    assert growth > 1e6, growth
+    assert a1.abs().max().item() <= 1.01
