@@ -287,6 +287,8 @@ def run_ours(args, rank, world, local_rank):
             "l2_error_vs_fp64": err,
             "fp64_per_element": fp64,
             "device_status": status}
+    if not args.no_configs:
+        line["configs"] = secondary_configs(sl, torch, flush, quick=args.quick_configs)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n, seconds=args.ref_seconds)
     print(json.dumps(line), flush=True)
@@ -294,6 +296,68 @@ def run_ours(args, rank, world, local_rank):
 
 # DRAM bytes per launch from one ncu capture of the same workload (None once the kernel changed)
 TRAFFIC = {}
+
+
+def _problem_state(sl, torch, prob, precision):
+    """Context and initial state (device doubles) of a workload."""
+    ctx = sl.Context(prob.dim, prob.kx, prob.ky, prob.box, prob.n, prob.basis, precision, prob.bc, prob.ghost)
+    x, y = ctx.node_coords()
+    phi = prob.phi0(x) if prob.dim == 1 else prob.phi0(x, y)
+    return ctx, torch.tensor(np.ascontiguousarray(phi).ravel(), device="cuda")
+
+
+def measure_config(sl, torch, prob, precision, steps, flush, phi=None):
+    """Per-step CUDA-event time of one workload on one path (L2 flushed before each step)."""
+    ctx, phi0 = _problem_state(sl, torch, prob, precision) if phi is None else (
+        sl.Context(prob.dim, prob.kx, prob.ky, prob.box, prob.n, prob.basis, precision, prob.bc, prob.ghost), phi)
+    vel = sl.velocity(prob.velocity.kind, *prob.velocity.p)
+    dt = ctx.max_dt(vel, sl_inputs.rule_code(prob))
+    opts = sl.options(prob.constraints, prob.rk_order)
+    a, b = ctx.pack(phi0), ctx.new_state()
+    stream = ctx.stream
+    ctx.step(a, b, vel, 0.0, dt, opts)           # warm-up
+    torch.cuda.synchronize()
+    ms, a, b, _ = _time_steps(torch, ctx, stream, b, a, vel, dt, opts, dt, steps, flush)
+    status = ctx.sync()
+    out = ctx.unpack(a)
+    nodes = ctx.size
+    per = ms / steps
+    return {"ms_per_step": per, "node_updates_per_s": nodes / (per * 1e-3), "steps": steps,
+            "hbm_frac_of_measured": nodes * 16 / (per * 1e-3) / 1e9 / peaks()[0], "device_status": status}, phi0, out, (
+        ctx, vel, dt, opts)
+
+
+def secondary_configs(sl, torch, flush, quick=False):
+    """Every configuration of the measurement plan on both paths, outside the headline timed region."""
+    res = []
+    plan = [("1d_sine_K16_n9 (config 1)", sl_inputs.config1_1d_sine(), [sl.FP64], 200)]
+    for n in (5, 9, 13, 17):
+        plan.append((f"1d_gauss_K2^20_n{n} (config 2)", sl_inputs.config2_1d_gauss(n), [sl.MIXED, sl.FP64], 50))
+    plan.append(("2d_const_512x512_n9 (config 3)", sl_inputs.config3_2d_const(), [sl.MIXED, sl.FP64], 10))
+    if not quick:
+        plan.append(("2d_swirl_2048x2048_n8 (config 5)", sl_inputs.config5_swirl(), [sl.MIXED, sl.FP64], 3))
+    for name, prob, precs, steps in plan:
+        entry = {"workload": name, "nodes": None}
+        phi0, outs = None, {}
+        for prec in precs:
+            r, phi0, out, run = measure_config(sl, torch, prob, prec, steps, flush, phi0)
+            key = "mixed" if prec == sl.MIXED else "fp64"
+            entry[key] = r
+            entry["nodes"] = int(phi0.numel())
+            # one step from the initial state for the accuracy comparison
+            ctx, vel, dt, opts = run
+            a, b = ctx.pack(phi0), ctx.new_state()
+            ctx.step(a, b, vel, 0.0, dt, opts)
+            outs[key] = ctx.unpack(b)
+            del ctx, a, b
+        if "mixed" in outs and "fp64" in outs:
+            d = outs["mixed"] - outs["fp64"]
+            entry["mixed_vs_fp64_rel_l2_after_1_step"] = float((d.norm() / outs["fp64"].norm()).item())
+            entry["mixed_speedup_over_fp64"] = entry["fp64"]["ms_per_step"] / entry["mixed"]["ms_per_step"]
+        del outs, phi0
+        torch.cuda.empty_cache()
+        res.append(entry)
+    return res
 
 
 def main():
@@ -308,6 +372,8 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-element comparison")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configurations")
+    ap.add_argument("--quick-configs", action="store_true", help="other configurations without the 2048^2 one")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
