@@ -1,0 +1,141 @@
+// Host construction (long double) of the shared 2D step operator for a uniform mesh under a
+// constant velocity (a, b): every element then sees the same advected geometry (Sec. 5.3), so the
+// remap (eq. 5.4, separable: A_y (x) A_x), the face traces (eq. 2dx/2dy_bnd_interpolate), the
+// upwind values (eq. 4.12a), the mass target (eq. remap_mass with the RK quadrature of the face
+// flux) and the constrained fit (eq. matrix_a) reduce to a few small operators applied per
+// element in structured form:
+//   psihat = R_y psi R_x^T                        (separable remap, R = A^{-1} of a uniform shift)
+//   trace of the x-upwind neighbour, row j   = sum_m R_y[j][m] sum_q psi_X[m][q] r_ox[q]
+//   trace of the y-upwind neighbour, col i   = sum_p R_x[i][p] sum_q r_oy[q] psi_Y[q][p]
+//   mass target (reference measure)          = K_self . psi + K_x . psi_X + K_y . psi_Y
+//   phi_L = psihat + C+_sub r, r = residuals of the inflow-face rows and the mass row (the
+//   outflow-face rows meet their targets exactly: they are this element's own traces).
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "sl_internal.h"
+
+namespace sl {
+namespace {
+using ld = long double;
+
+std::vector<ld> basis_at(const std::vector<ld>& nodes, ld z) {
+  const int n = (int)nodes.size();
+  std::vector<ld> v(n, 1.0L);
+  for (int j = 0; j < n; ++j)
+    for (int m = 0; m < n; ++m)
+      if (m != j) v[j] *= (z - nodes[m]) / (nodes[j] - nodes[m]);
+  return v;
+}
+
+}  // namespace
+
+bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigned cons, int rk,
+                         std::vector<float>& buf, Mixed2DConstParams& P, std::string& err) {
+  const int n = c->n, nd = n * n;
+  const Basis1D& B = c->b;
+  const double hx = (c->mesh.x1 - c->mesh.x0) / c->mesh.kx, hy = (c->mesh.y1 - c->mesh.y0) / c->mesh.ky;
+  if (a == 0.0 || b == 0.0) { err = "the 2D shared-operator path needs both velocity components non-zero"; return false; }
+  if (cons & SL_C_ENERGY) { err = "energy is applied by the general 2D mixed path"; return false; }
+  std::vector<ld> xi(B.xi.begin(), B.xi.end()), w(B.w.begin(), B.w.end());
+  const ld dx = (ld)a * dt / hx, dy = (ld)b * dt / hy;
+  // remap matrices R[l][q] = l_q(xi_l - shift)
+  std::vector<ld> Rx(nd), Ry(nd);
+  for (int l = 0; l < n; ++l) {
+    std::vector<ld> vx = basis_at(xi, xi[l] - dx), vy = basis_at(xi, xi[l] - dy);
+    for (int q = 0; q < n; ++q) { Rx[l * n + q] = vx[q]; Ry[l * n + q] = vy[q]; }
+  }
+  const bool xw = a > 0.0, ys = b > 0.0;       // x-upwind neighbour is W (else E); y-upwind is S (else N)
+  std::vector<ld> l0 = basis_at(xi, 0.0L), l1 = basis_at(xi, 1.0L);
+  const std::vector<ld>& lin_x = xw ? l0 : l1;
+  const std::vector<ld>& lout_x = xw ? l1 : l0;
+  const std::vector<ld>& lin_y = ys ? l0 : l1;
+  const std::vector<ld>& lout_y = ys ? l1 : l0;
+  std::vector<ld> r_ox(n, 0.0L), r_oy(n, 0.0L);
+  for (int q = 0; q < n; ++q)
+    for (int i = 0; i < n; ++i) {
+      r_ox[q] += Rx[i * n + q] * lout_x[i];
+      r_oy[q] += Ry[i * n + q] * lout_y[i];
+    }
+  // outflow-face flux functionals (mass): Kx[m][l] = |a| hy sum_s b_s sum_q w_q l_m(eta_q - c dy) l_l(xo - c dx)
+  static const double rkb[5][4] = {{}, {1.0}, {0.5, 0.5}, {1.0 / 6, 2.0 / 3, 1.0 / 6}, {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}};
+  static const double rkc[5][4] = {{}, {0.0}, {0.0, 1.0}, {0.0, 0.5, 1.0}, {0.0, 0.5, 0.5, 1.0}};
+  std::map<double, ld> stages;
+  for (int s = 0; s < rk; ++s) stages[rkc[rk][s]] += (ld)rkb[rk][s];
+  std::vector<ld> Kx(nd, 0.0L), Ky(nd, 0.0L);
+  const ld xo = xw ? 1.0L : 0.0L, yo = ys ? 1.0L : 0.0L;
+  for (auto& kv : stages) {
+    const ld cs = kv.first, bs = kv.second;
+    std::vector<ld> ex = basis_at(xi, xo - cs * dx), ey = basis_at(xi, yo - cs * dy);
+    for (int q = 0; q < n; ++q) {
+      std::vector<ld> ty = basis_at(xi, xi[q] - cs * dy), tx = basis_at(xi, xi[q] - cs * dx);
+      for (int m = 0; m < n; ++m)
+        for (int l = 0; l < n; ++l) {
+          Kx[m * n + l] += std::fabs((ld)a) * hy * bs * w[q] * ty[m] * ex[l];
+          Ky[m * n + l] += std::fabs((ld)b) * hx * bs * w[q] * ey[m] * tx[l];
+        }
+    }
+  }
+  const ld lam = (ld)dt / ((ld)hx * hy);
+  // rows of the hard fit: W (n), E (n), S (n), N (n), mass (1) -- see make_fit_2d
+  const FitOps& F = c->fit[cons & 3u][0];
+  const int m = F.m;
+  const bool bnd = cons & SL_C_BOUNDARY, mass = cons & SL_C_MASS;
+  std::vector<int> cols;                         // columns of C+ kept: inflow x rows, inflow y rows, mass
+  if (bnd) {
+    const int fx = xw ? 0 : 1, fy = ys ? 2 : 3;
+    for (int q = 0; q < n; ++q) cols.push_back(fx * n + q);
+    for (int q = 0; q < n; ++q) cols.push_back(fy * n + q);
+  }
+  if (mass) cols.push_back(bnd ? 4 * n : 0);
+  const int mc = (int)cols.size();
+  // float buffer layout
+  P = Mixed2DConstParams{};
+  P.n = n;
+  P.kx = c->mesh.kx;
+  P.ky = c->mesh.ky;
+  P.xw = xw ? 1 : 0;
+  P.ys = ys ? 1 : 0;
+  P.per_x = c->mesh.bc[0] == SL_BC_PERIODIC ? 1 : 0;
+  P.per_y = c->mesh.bc[2] == SL_BC_PERIODIC ? 1 : 0;
+  P.ghost = c->mesh.ghost;
+  P.bnd = bnd ? 1 : 0;
+  P.mass = mass ? 1 : 0;
+  P.mc = mc;
+  P.flux_x = (float)(lam * std::fabs((ld)a) * hy);    // K_x applied to a constant c gives c |a| hy
+  P.flux_y = (float)(lam * std::fabs((ld)b) * hx);
+  buf.clear();
+  auto put = [&](const std::vector<ld>& v) {
+    size_t off = buf.size();
+    for (ld x : v) buf.push_back((float)x);
+    return (int)off;
+  };
+  P.o_Rx = put(Rx);
+  P.o_Ry = put(Ry);
+  P.o_linx = put(lin_x);
+  P.o_liny = put(lin_y);
+  P.o_rox = put(r_ox);
+  P.o_roy = put(r_oy);
+  std::vector<ld> Kself(nd), Kxl(nd), Kyl(nd), W2(nd);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      const int k = j * n + i;
+      W2[k] = w[j] * w[i];
+      Kself[k] = W2[k] - lam * (Kx[k] + Ky[k]);
+      Kxl[k] = lam * Kx[k];
+      Kyl[k] = lam * Ky[k];
+    }
+  P.o_kself = put(Kself);
+  P.o_kx = put(Kxl);
+  P.o_ky = put(Kyl);
+  P.o_w2 = put(W2);
+  std::vector<ld> Cs(nd * std::max(mc, 1), 0.0L);
+  for (int r = 0; r < nd; ++r)
+    for (int k = 0; k < mc; ++k) Cs[r * mc + k] = (ld)F.Cpinv[r * m + cols[k]];
+  P.o_cp = put(Cs);
+  buf.resize((buf.size() + 3) & ~size_t(3), 0.0f);
+  return true;
+}
+
+}  // namespace sl

@@ -189,6 +189,7 @@ void sl_free(sl_ctx* c) {
   cudaFree(c->d_io64);
   cudaFree(c->d_work);
   cudaFree(c->d_ftab);
+  cudaFree(c->d_m2c);
   delete c;
 }
 
@@ -268,6 +269,36 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
     Tables1D tb{T + c->off_xi, T + c->off_w, T + c->off_lam, T + c->off_l0, T + c->off_l1,
                 T + off[0], T + off[1], T + off[2]};
     launch_step2d_f64(c->n, P, tb, (const double*)phi_in, (double*)phi_out, c->d_work, c->d_status, c->stream);
+  } else if (M.dim == 2 && c->precision == SL_MIXED && vel->kind == SL_VEL_CONST && vel->p[0] != 0.0 &&
+             vel->p[1] != 0.0 && opt->fit == SL_FIT_HARD && !(opt->constraints & SL_C_ENERGY) &&
+             opt->bvalue == SL_BV_INTERP && (opt->constraints & 3u)) {
+    // uniform mesh, constant velocity: one operator shared by all elements
+    if (!c->m2c_valid || c->m2c_a != vel->p[0] || c->m2c_b != vel->p[1] || c->m2c_dt != dt ||
+        c->m2c_cons != opt->constraints || c->m2c_rk != opt->rk_order) {
+      std::string why;
+      if (!build_mixed2d_const(c, vel->p[0], vel->p[1], dt, opt->constraints, opt->rk_order, c->m2c_host, c->m2c, why))
+        return fail(c, SL_EUNSUPPORTED, why);
+      if (c->m2c_host.size() > c->m2c_cap) {
+        cudaFree(c->d_m2c);
+        c->d_m2c = nullptr;
+        c->m2c_cap = 0;
+        if (cudaMalloc(&c->d_m2c, c->m2c_host.size() * sizeof(float)) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(c, SL_ENOMEM, "device allocation of the shared operator failed");
+        }
+        c->m2c_cap = c->m2c_host.size();
+      }
+      SL_CUDA(c, cudaMemcpyAsync(c->d_m2c, c->m2c_host.data(), c->m2c_host.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, c->stream));
+      c->m2c_valid = true;
+      c->m2c_a = vel->p[0];
+      c->m2c_b = vel->p[1];
+      c->m2c_dt = dt;
+      c->m2c_cons = opt->constraints;
+      c->m2c_rk = opt->rk_order;
+    }
+    c->m2c.plane = plane_stride(c->nvals);
+    launch_step2d_const(c->m2c, c->d_m2c, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream);
   } else if (M.dim == 2 && c->precision == SL_MIXED) {
     if (opt->bvalue != SL_BV_INTERP)
       return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");

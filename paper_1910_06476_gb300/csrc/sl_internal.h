@@ -102,6 +102,20 @@ void launch_step2d_mixed(int n, const StepParams& p, const Mixed2DExtra& x, cons
                          unsigned* status, cudaStream_t s);
 inline int64_t work2m_floats(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 16 + 4); }
 
+// Parameters of the 2D shared-operator kernel (uniform mesh, constant velocity); the operators
+// live in a float table at the given offsets
+struct Mixed2DConstParams {
+  int n, kx, ky, xw, ys, per_x, per_y, bnd, mass, mc;
+  double ghost;
+  float flux_x, flux_y;
+  int64_t plane;
+  int o_Rx, o_Ry, o_linx, o_liny, o_rox, o_roy, o_kself, o_kx, o_ky, o_w2, o_cp;
+};
+bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigned cons, int rk,
+                         std::vector<float>& buf, Mixed2DConstParams& P, std::string& err);
+void launch_step2d_const(const Mixed2DConstParams& p, const float* tab, const float* in, float* out, unsigned* status,
+                         cudaStream_t s);
+
 // Kernel parameter block of the 1D shared-operator (mixed precision) step; passed by value.
 struct Mixed1DParams {
   int n, K, left_up, periodic, m, mass_on, energy_on, nst;
@@ -157,6 +171,15 @@ struct sl_ctx {
   double* d_io64 = nullptr;
   double* d_work = nullptr;              // 2D workspace between the two phases
   float* d_ftab = nullptr;               // float tables of the mixed 2D path
+  // cached shared operator of the mixed 2D constant-velocity path
+  bool m2c_valid = false;
+  double m2c_a = 0, m2c_b = 0, m2c_dt = 0;
+  unsigned m2c_cons = 0;
+  int m2c_rk = 0;
+  std::vector<float> m2c_host;
+  float* d_m2c = nullptr;
+  size_t m2c_cap = 0;
+  sl::Mixed2DConstParams m2c{};
   size_t f_off[5] = {};                  // xi, lam, w, l0, l1
   size_t f_cp[4] = {};                   // float pseudo-inverse per linear-row mask
   // cached shared operator of the mixed 1D path, keyed on (a, dt, constraints, rk, fit)

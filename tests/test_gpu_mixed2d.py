@@ -41,6 +41,14 @@ CASES = [
     (5, 5, 8, 2, (5.0,), 1, 7, 4, "sincos"),
     (3, 3, 12, 1, (2 * np.pi, 0.5, 0.5), 1, 3, 3, "sincos"),
     (2, 2, 16, 0, (0.6, 0.9), 0, 3, 4, "sincos"),
+    # constant velocity without energy runs the shared-operator kernel: ragged tiles, inflow
+    # ghost faces, every tile shape, mass only and boundary only
+    (9, 5, 9, 0, (0.7, -0.45), 0, 3, 4, "sincos"),
+    (11, 6, 5, 0, (-0.9, 0.6), 1, 3, 4, "sincos"),
+    (5, 5, 11, 0, (0.5, 0.8), 0, 3, 3, "sincos"),
+    (5, 3, 13, 0, (-0.6, -0.7), 1, 3, 4, "sincos"),
+    (3, 3, 17, 0, (0.6, 0.9), 0, 2, 4, "sincos"),
+    (7, 4, 4, 0, (0.6, 0.9), 0, 1, 2, "sincos"),
 ]
 
 DATA = {"sincos": lambda x, y: 1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y),
