@@ -111,8 +111,18 @@ bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigne
     for (ld x : v) buf.push_back((float)x);
     return (int)off;
   };
+  // threads read their own row of several tables: those are stored transposed ([col][row]) so
+  // that the n threads of an element read n consecutive floats
+  auto transpose = [n](const std::vector<ld>& M) {
+    std::vector<ld> T(M.size());
+    for (int r = 0; r < n; ++r)
+      for (int q = 0; q < n; ++q) T[q * n + r] = M[r * n + q];
+    return T;
+  };
   P.o_Rx = put(Rx);
   P.o_Ry = put(Ry);
+  P.o_RxT = put(transpose(Rx));
+  P.o_RyT = put(transpose(Ry));
   P.o_linx = put(lin_x);
   P.o_liny = put(lin_y);
   P.o_rox = put(r_ox);
@@ -126,13 +136,15 @@ bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigne
       Kxl[k] = lam * Kx[k];
       Kyl[k] = lam * Ky[k];
     }
-  P.o_kself = put(Kself);
-  P.o_kx = put(Kxl);
-  P.o_ky = put(Kyl);
-  P.o_w2 = put(W2);
+  P.o_kself = put(transpose(Kself));
+  P.o_kx = put(transpose(Kxl));
+  P.o_ky = put(transpose(Kyl));
+  P.o_w2 = put(transpose(W2));
+  // C+ restricted to the kept columns, as Cs[(l * mc + k) * n + j] for output node (j, l)
   std::vector<ld> Cs(nd * std::max(mc, 1), 0.0L);
-  for (int r = 0; r < nd; ++r)
-    for (int k = 0; k < mc; ++k) Cs[r * mc + k] = (ld)F.Cpinv[r * m + cols[k]];
+  for (int j = 0; j < n; ++j)
+    for (int l = 0; l < n; ++l)
+      for (int k = 0; k < mc; ++k) Cs[(l * mc + k) * n + j] = (ld)F.Cpinv[(j * n + l) * m + cols[k]];
   P.o_cp = put(Cs);
   buf.resize((buf.size() + 3) & ~size_t(3), 0.0f);
   return true;

@@ -109,7 +109,7 @@ struct Mixed2DConstParams {
   double ghost;
   float flux_x, flux_y;
   int64_t plane;
-  int o_Rx, o_Ry, o_linx, o_liny, o_rox, o_roy, o_kself, o_kx, o_ky, o_w2, o_cp;
+  int o_Rx, o_Ry, o_RxT, o_RyT, o_linx, o_liny, o_rox, o_roy, o_kself, o_kx, o_ky, o_w2, o_cp;
 };
 bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigned cons, int rk,
                          std::vector<float>& buf, Mixed2DConstParams& P, std::string& err);
