@@ -69,7 +69,7 @@ __device__ __forceinline__ void copy_run(const float* __restrict__ in, int64_t p
 }
 
 template <int NN, int TX, int TY>
-__global__ void __launch_bounds__(Tile<NN, TX, TY>::NT) k_step(const __grid_constant__ Mixed2DConstParams P,
+__global__ void __launch_bounds__(Tile<NN, TX, TY>::NT) k_step2d_shared(const __grid_constant__ Mixed2DConstParams P,
                                                                const float* __restrict__ tab,
                                                                const float* __restrict__ in, float* __restrict__ out,
                                                                unsigned* status) {
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT) k_step(const __grid_cons
 template <int NN, int TX, int TY>
 void launch(const Mixed2DConstParams& p, const float* tab, const float* in, float* out, unsigned* st, cudaStream_t s) {
   dim3 grid((p.kx + TX - 1) / TX, (p.ky + TY - 1) / TY);
-  k_step<NN, TX, TY><<<grid, Tile<NN, TX, TY>::NT, 0, s>>>(p, tab, in, out, st);
+  k_step2d_shared<NN, TX, TY><<<grid, Tile<NN, TX, TY>::NT, 0, s>>>(p, tab, in, out, st);
 }
 
 }  // namespace k2c
