@@ -1,19 +1,21 @@
 #pragma once
 // 2D DSEM-SL step, mixed precision, shared operator: uniform mesh and constant velocity (a, b), so
 // every element sees the same advected geometry (Sec. 5.3).  Operators are built once on the host
-// (ops_mixed2d.cpp) and applied here in structured form, n threads per element (thread j owns row
-// j of the element's n x n nodes):
-//   x-remap of row j, then y-remap through shared memory      psihat = R_y psi R_x^T   (eq. 5.4)
-//   own traces at the inflow faces and the upwind neighbours' traces     (eq. 2dx/2dy, 4.12a)
-//   mass target from the outflow-face flux functionals                   (eq. remap_mass)
-//   constrained fit restricted to the inflow-face rows and the mass row  (eq. matrix_a)
+// (ops_mixed2d.cpp) and applied here in structured form, n threads per element:
+//   row phase (thread j owns row j): x-remap of the row, x inflow residual pieces, y-neighbour
+//     outflow functional, mass residual pieces                      (eq. 5.4, 4.12a, remap_mass)
+//   column phase (thread j owns column j): y-remap of the column, inflow residuals
+//   fit: s = (C C^T)^+ r over the inflow-face and mass rows, phi_L = psihat + C^T s   (eq. matrix_a)
+// C^T s is separable (face rows are l0/l1 along one index and a unit vector along the other, the
+// mass row is w (x) w), so the constrained fit costs O(n) per node instead of O(n) per constraint.
+// Operators applied with the same entry by every thread are read from the parameter bank.
 // State is double-float (hi plane, lo plane); all arithmetic is in float on increments relative to
 // the element's first hi value and the result is written back exactly (TwoSum).
 //
-// A CTA owns a TX x TY tile of elements.  Staging slots are laid out row by row with the x-upwind
-// halo element next to its row, so each staged row is one contiguous run of global memory (moved
-// with aligned 16-byte vectors), followed by the y-upwind halo row.  Tables that a thread reads by
-// its own row are stored transposed, so an element's n threads read consecutive floats.
+// A CTA owns a TX x TY tile of elements.  Each staged tile row (the TX elements plus the x-upwind
+// halo element) is one contiguous run of global memory; it is copied in aligned 16-byte vectors
+// into a shared row buffer at the same offset modulo 16 bytes, followed by the y-upwind halo row.
+// Results are written back into the own slots and stored from there with aligned vectors.
 #include "sl_internal.h"
 
 namespace sl {
@@ -24,9 +26,12 @@ struct Tile {
   static constexpr int ND = NN * NN;
   static constexpr int NE = TX * TY;              // elements advanced by one CTA
   static constexpr int RW = TX + 1;               // slots per staged tile row (with the x halo)
-  static constexpr int NS = TY * RW + TX;         // staged elements (+ the y halo row)
+  static constexpr int RS = (RW * ND + 8 + 3) & ~3;   // floats per staged row buffer (16-byte multiple)
+  static constexpr int HS = (TX * ND + 8 + 3) & ~3;   // floats of the y-halo row buffer
+  static constexpr int SP = TY * RS + HS;         // floats per staged plane
+  static constexpr int VR = RS / 4, VH = HS / 4, VT = TY * VR + VH;   // 16-byte vectors
   static constexpr int NT = NE * NN;              // threads
-  static constexpr int NR = 2 * NN + 1;           // residuals kept: inflow x rows, inflow y rows, mass
+  static constexpr int MAXV = (VT + NT - 1) / NT; // vectors per thread and plane
 };
 
 __device__ __forceinline__ int wrapi(int i, int n, bool per) {
@@ -36,210 +41,258 @@ __device__ __forceinline__ int wrapi(int i, int n, bool per) {
   return i < 0 ? i + n : i;
 }
 
-// Copy cnt contiguous floats of each plane, starting at global float g0, to shared memory at s0;
-// the global window is rounded out to 16-byte boundaries (the planes are 256-byte aligned and the
-// state buffer ends on a 64-float boundary).
-template <int NT, int MAXV>
-__device__ __forceinline__ void copy_run(const float* __restrict__ in, int64_t plane, int64_t g0, int cnt, float* shi,
-                                         float* slo, int s0, int tid) {
-  const int64_t a0 = g0 & ~int64_t(3);
-  const int nvec = (int)(((g0 + cnt + 3) & ~int64_t(3)) - a0) >> 2;
-  const int off = (int)(g0 - a0);
-  const float4* ih = reinterpret_cast<const float4*>(in + a0);
-  const float4* il = reinterpret_cast<const float4*>(in + plane + a0);
-  float4 vh[MAXV], vl[MAXV];
-#pragma unroll
-  for (int k = 0; k < MAXV; ++k) {
-    const int v = tid + k * NT;
-    if (v < nvec) { vh[k] = __ldg(ih + v); vl[k] = __ldg(il + v); }
-  }
-#pragma unroll
-  for (int k = 0; k < MAXV; ++k) {
-    const int v = tid + k * NT;
-    if (v < nvec) {
-      const float h4[4] = {vh[k].x, vh[k].y, vh[k].z, vh[k].w};
-      const float l4[4] = {vl[k].x, vl[k].y, vl[k].z, vl[k].w};
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int q = 4 * v + c - off;           // float index within the run
-        if (q >= 0 && q < cnt) { shi[s0 + q] = h4[c]; slo[s0 + q] = l4[c]; }
-      }
-    }
-  }
-}
+__device__ __forceinline__ int64_t floor4(int64_t g) { return g & ~int64_t(3); }
 
 template <int NN, int TX, int TY>
-__global__ void __launch_bounds__(Tile<NN, TX, TY>::NT) k_step2d_shared(const __grid_constant__ Mixed2DConstParams P,
-                                                               const float* __restrict__ tab,
-                                                               const float* __restrict__ in, float* __restrict__ out,
-                                                               unsigned* status) {
+__global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
+    k_step2d_shared(const __grid_constant__ Mixed2DConstParams P, const float* __restrict__ tab,
+                    const float* __restrict__ in, float* __restrict__ out, unsigned* status) {
   using T = Tile<NN, TX, TY>;
-  constexpr int ND = T::ND, NE = T::NE, RW = T::RW, NS = T::NS, NT = T::NT, NR = T::NR;
-  constexpr int MAXV = ((RW * ND + 8) / 4 + NT - 1) / NT;
-  __shared__ float s_hi[NS * ND];
-  __shared__ float s_lo[NS * ND];
-  __shared__ float s_t[NE * ND];                  // x-remapped rows, then psihat
-  __shared__ float s_gx[NE][NN], s_gy[NE][NN], s_p[NE][NN], s_r[NE][NR];
-  __shared__ int s_ge[NS];                        // global element of each staged slot (-1: ghost)
+  constexpr int ND = T::ND, NE = T::NE, RW = T::RW, RS = T::RS, SP = T::SP, NT = T::NT;
+  constexpr int VR = T::VR, VT = T::VT, MAXV = T::MAXV;
+  __shared__ __align__(16) float s_hi[SP];
+  __shared__ __align__(16) float s_lo[SP];
+  __shared__ float s_t[NE * ND];                  // x-remapped rows
+  __shared__ float s_dx[NE][NN], s_v[NE][NN], s_p[NE][NN], s_r[NE][2 * NN], s_sw[NE][NN], s_se[NE][NN];
+  __shared__ int64_t s_a0[TY + 1];                // first aligned global float of each staged row
+  __shared__ int s_off[TY + 1], s_nv[TY + 1];     // row data offset in its buffer; vectors (0: gather)
   const int tid = threadIdx.x;
   const int ex0 = blockIdx.x * TX, ey0 = blockIdx.y * TY;
   const bool perx = P.per_x != 0, pery = P.per_y != 0;
   const int xs0 = P.xw ? ex0 - 1 : ex0;           // first element of a staged tile row
-  // slot -> global element
-  if (tid < NS) {
-    int ex, ey;
-    if (tid < TY * RW) { ex = xs0 + tid % RW; ey = ey0 + tid / RW; }
-    else { ex = ex0 + (tid - TY * RW); ey = P.ys ? ey0 - 1 : ey0 + TY; }
-    const int wx = wrapi(ex, P.kx, perx), wy = wrapi(ey, P.ky, pery);
-    s_ge[tid] = (wx < 0 || wy < 0) ? -1 : wy * P.kx + wx;
+  const int eyh = P.ys ? ey0 - 1 : ey0 + TY;      // element row of the y halo
+  if (tid <= TY) {
+    const int ey = tid < TY ? ey0 + tid : eyh;
+    const int xa = tid < TY ? xs0 : ex0, cnt = tid < TY ? RW : TX;
+    const int64_t g0 = ((int64_t)ey * P.kx + xa) * ND;
+    const int64_t a0 = floor4(g0);
+    const bool fast = ey >= 0 && ey < P.ky && xa >= 0 && xa + cnt <= P.kx;
+    s_a0[tid] = a0;
+    s_off[tid] = (int)(g0 - a0);
+    s_nv[tid] = fast ? (int)((floor4(g0 + cnt * ND + 3) - a0) >> 2) : 0;
   }
   __syncthreads();
-  // staged rows: contiguous global runs when they need no wrap, else element by element
-  const int yrow = P.ys ? ey0 - 1 : ey0 + TY;
+  // contiguous rows: every vector load first, then the shared stores
+  {
+    float4 vh[MAXV], vl[MAXV];
 #pragma unroll
-  for (int r = 0; r <= TY; ++r) {
-    const int ey = r < TY ? ey0 + r : yrow;
-    const int xa = r < TY ? xs0 : ex0, cntx = r < TY ? RW : TX;
-    const int s0 = r < TY ? r * RW : TY * RW;
-    const bool fast = ey >= 0 && ey < P.ky && xa >= 0 && xa + cntx <= P.kx;
-    if (fast) {
-      copy_run<NT, MAXV>(in, P.plane, ((int64_t)ey * P.kx + xa) * ND, cntx * ND, s_hi, s_lo, s0 * ND, tid);
-    } else {
-      for (int idx = tid; idx < cntx * ND; idx += NT) {
-        const int slot = s0 + idx / ND, q = idx % ND;
-        const int g = s_ge[slot];
-        s_hi[slot * ND + q] = g >= 0 ? __ldg(in + (size_t)g * ND + q) : 0.0f;
-        s_lo[slot * ND + q] = g >= 0 ? __ldg(in + P.plane + (size_t)g * ND + q) : 0.0f;
+    for (int k = 0; k < MAXV; ++k) {
+      const int v = tid + k * NT;
+      const int r = v < TY * VR ? v / VR : TY;
+      const int vv = v - r * VR;
+      if (v < VT && vv < s_nv[r]) {
+        const float4* src = reinterpret_cast<const float4*>(in + s_a0[r]) + vv;
+        vh[k] = __ldg(src);
+        vl[k] = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(src) + P.plane));
       }
+    }
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      const int v = tid + k * NT;
+      const int r = v < TY * VR ? v / VR : TY;
+      const int vv = v - r * VR;
+      if (v < VT && vv < s_nv[r]) {
+        reinterpret_cast<float4*>(s_hi + r * RS)[vv] = vh[k];
+        reinterpret_cast<float4*>(s_lo + r * RS)[vv] = vl[k];
+      }
+    }
+  }
+  // rows that wrap, leave the mesh or are ragged: element by element (ghost slots hold zero)
+#pragma unroll 1
+  for (int r = 0; r <= TY; ++r) {
+    if (s_nv[r] != 0) continue;
+    const int ey = r < TY ? ey0 + r : eyh;
+    const int xa = r < TY ? xs0 : ex0, cnt = r < TY ? RW : TX;
+    const int wy = wrapi(ey, P.ky, pery);
+    const int base = r * RS + s_off[r];
+    for (int idx = tid; idx < cnt * ND; idx += NT) {
+      const int sl = idx / ND, q = idx - sl * ND;
+      const int wx = wrapi(xa + sl, P.kx, perx);
+      const bool ok = wx >= 0 && wy >= 0;
+      const size_t g = ((size_t)wy * P.kx + wx) * ND + q;
+      s_hi[base + idx] = ok ? __ldg(in + g) : 0.0f;
+      s_lo[base + idx] = ok ? __ldg(in + P.plane + g) : 0.0f;
     }
   }
   __syncthreads();
 
-  const int el = tid / NN, j = tid % NN;          // element in the tile, row
+  const int el = tid / NN, j = tid - (tid / NN) * NN;   // element in the tile, row / column index
   const int lx = el % TX, ly = el / TX;
-  const bool active = (ex0 + lx < P.kx) && (ey0 + ly < P.ky);
-  const int so = ly * RW + lx + P.xw;             // own slot
-  const int sx = P.xw ? so - 1 : so + 1;          // x-upwind neighbour (the halo is in the row)
-  const int sy = P.ys ? (ly > 0 ? so - RW : TY * RW + lx) : (ly < TY - 1 ? so + RW : TY * RW + lx);
-  const bool gx = s_ge[sx] < 0, gy = s_ge[sy] < 0;
-  const float* Rx = tab + P.o_Rx;
-  const float* RxT = tab + P.o_RxT;
-  const float* RyT = tab + P.o_RyT;
-  const float ref = s_hi[so * ND];
+  const int ex = ex0 + lx, ey = ey0 + ly;
+  const bool active = ex < P.kx && ey < P.ky;
+  // own slot, x-upwind neighbour (same staged row), y-upwind neighbour (adjacent row or the halo)
+  const int so = ly * RS + s_off[ly] + (lx + P.xw) * ND;
+  const int sx = ly * RS + s_off[ly] + (P.xw ? lx : lx + 1) * ND;
+  const int ry = P.ys ? ly - 1 : ly + 1;
+  const int sy = (ry >= 0 && ry < TY) ? ry * RS + s_off[ry] + (lx + P.xw) * ND : TY * RS + s_off[TY] + lx * ND;
+  const bool gx = wrapi(P.xw ? ex - 1 : ex + 1, P.kx, perx) < 0;
+  const bool gy = wrapi(P.ys ? ey - 1 : ey + 1, P.ky, pery) < 0;
+  const float ref = s_hi[so];
   const float gval = (float)(P.ghost - (double)ref);
-  float ps[NN], px[NN];
-#pragma unroll
-  for (int i = 0; i < NN; ++i) {
-    ps[i] = (s_hi[so * ND + j * NN + i] - ref) + s_lo[so * ND + j * NN + i];
-    px[i] = gx ? gval : (s_hi[sx * ND + j * NN + i] - ref) + s_lo[sx * ND + j * NN + i];
-  }
-  // x-remap of row j (every thread reads the same R_x entry: a broadcast)
-#pragma unroll
-  for (int l = 0; l < NN; ++l) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int i = 0; i < NN; ++i) acc = fmaf(__ldg(Rx + l * NN + i), ps[i], acc);
-    s_t[el * ND + j * NN + l] = acc;
-  }
-  // x-upwind neighbour row functional, y-upwind neighbour column functional, mass target row j
+
+  // ---- row phase: thread j holds row j of psi and psi_X, column j of psi_Y
+  float ps[NN];
   {
-    float u = 0.0f, v = 0.0f, pm = 0.0f;
-#pragma unroll
-    for (int q = 0; q < NN; ++q) {
-      u = fmaf(px[q], __ldg(tab + P.o_rox + q), u);
-      const float yq = gy ? gval : (s_hi[sy * ND + q * NN + j] - ref) + s_lo[sy * ND + q * NN + j];
-      v = fmaf(__ldg(tab + P.o_roy + q), yq, v);
-    }
+    float px[NN], py[NN];
 #pragma unroll
     for (int i = 0; i < NN; ++i) {
-      const float yi = gy ? gval : (s_hi[sy * ND + j * NN + i] - ref) + s_lo[sy * ND + j * NN + i];
-      pm = fmaf(__ldg(tab + P.o_kself + i * NN + j), ps[i], pm);
-      pm = fmaf(__ldg(tab + P.o_kx + i * NN + j), px[i], pm);
-      pm = fmaf(__ldg(tab + P.o_ky + i * NN + j), yi, pm);
+      ps[i] = (s_hi[so + j * NN + i] - ref) + s_lo[so + j * NN + i];
+      px[i] = gx ? gval : (s_hi[sx + j * NN + i] - ref) + s_lo[sx + j * NN + i];
+      py[i] = gy ? gval : (s_hi[sy + i * NN + j] - ref) + s_lo[sy + i * NN + j];
     }
-    s_gx[el][j] = u;
-    s_gy[el][j] = v;
+    // x inflow residual pieces: upwind outflow trace minus own inflow trace, before the y-remap
+    float u = 0.0f, tau = 0.0f, v = 0.0f, pm = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NN; ++i) {
+      u = fmaf(P.rox[i], px[i], u);
+      tau = fmaf(P.xix[i], ps[i], tau);
+      v = fmaf(P.roy[i], py[i], v);
+    }
+    // mass residual pieces (target minus the mass of psihat, reference measure)
+    const float* Ks = tab + P.o_ks;
+    const float* Kx = tab + P.o_kx;
+    const float* Ky = tab + P.o_ky;
+#pragma unroll
+    for (int i = 0; i < NN; ++i) {
+      pm = fmaf(__ldg(Ks + i * NN + j), ps[i], pm);
+      pm = fmaf(__ldg(Kx + i * NN + j), px[i], pm);
+      pm = fmaf(__ldg(Ky + i * NN + j), py[i], pm);
+    }
+    s_dx[el][j] = (gx ? 0.0f : u) - tau;
+    s_v[el][j] = gy ? 0.0f : v;
     s_p[el][j] = pm;
   }
-  __syncthreads();
-  // y-remap: psihat row j = sum_q R_y[j][q] t[q][.]
-  float ph[NN];
-#pragma unroll
-  for (int l = 0; l < NN; ++l) ph[l] = 0.0f;
-#pragma unroll
-  for (int q = 0; q < NN; ++q) {
-    const float r = __ldg(RyT + q * NN + j);
-#pragma unroll
-    for (int l = 0; l < NN; ++l) ph[l] = fmaf(r, s_t[el * ND + q * NN + l], ph[l]);
-  }
-  // x inflow face, row j: upwind value minus own trace; mass of psihat row j
-  float trx = 0.0f, valx = 0.0f, mh = 0.0f;
+  // x-remap of row j: t[j][l] = sum_i R_x[l][i] psi[j][i]
 #pragma unroll
   for (int l = 0; l < NN; ++l) {
-    trx = fmaf(ph[l], __ldg(tab + P.o_linx + l), trx);
-    valx = fmaf(__ldg(RyT + l * NN + j), s_gx[el][l], valx);
-    mh = fmaf(__ldg(tab + P.o_w2 + l * NN + j), ph[l], mh);
-  }
-  if (gx) valx = gval;
-  __syncthreads();                                // every thread has read s_t: reuse it for psihat
-#pragma unroll
-  for (int l = 0; l < NN; ++l) s_t[el * ND + j * NN + l] = ph[l];
-  s_r[el][j] = valx - trx;
-  __syncthreads();
-  // y inflow face, column j: upwind value minus own trace
-  {
-    float tr = 0.0f, val = 0.0f;
-#pragma unroll
-    for (int m = 0; m < NN; ++m) {
-      tr = fmaf(s_t[el * ND + m * NN + j], __ldg(tab + P.o_liny + m), tr);
-      val = fmaf(__ldg(RxT + m * NN + j), s_gy[el][m], val);
-    }
-    if (gy) val = gval;
-    s_r[el][NN + j] = val - tr;
-  }
-  // mass residual: target minus the mass of psihat (row sums in index order)
-  s_p[el][j] -= mh;
-  __syncthreads();
-  if (j == 0) {
     float acc = 0.0f;
 #pragma unroll
-    for (int q = 0; q < NN; ++q) acc += s_p[el][q];
-    s_r[el][2 * NN] = acc;
+    for (int i = 0; i < NN; ++i) acc = fmaf(P.Rx[l * NN + i], ps[i], acc);
+    s_t[el * ND + j * NN + l] = acc;
   }
   __syncthreads();
-  // constrained fit: phi_L = psihat + C+_sub r over the kept rows
-  const int mc = P.mc;
-  const int r0 = P.bnd ? 0 : 2 * NN;               // without boundary rows only the mass residual
-  const float* Cp = tab + P.o_cp;
-  float res[NN];
+
+  // ---- column phase: thread j holds column j of psihat = R_y t
+  float ph[NN];
+  {
+    float tc[NN];
 #pragma unroll
-  for (int l = 0; l < NN; ++l) {
-    float acc = ph[l];
-    for (int k = 0; k < mc; ++k) acc = fmaf(__ldg(Cp + (l * mc + k) * NN + j), s_r[el][r0 + k], acc);
-    res[l] = acc;
-  }
-  // exact write-back (TwoSum) into this element's staging rows, then coalesced stores
-  bool finite = true;
+    for (int m = 0; m < NN; ++m) tc[m] = s_t[el * ND + m * NN + j];
 #pragma unroll
-  for (int l = 0; l < NN; ++l) {
-    const float s = ref + res[l];
-    const float bb = s - ref;
-    const float e = (ref - (s - bb)) + (res[l] - bb);
-    s_hi[so * ND + j * NN + l] = s;
-    s_lo[so * ND + j * NN + l] = e;
-    finite = finite && isfinite(s);
+    for (int k = 0; k < NN; ++k) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < NN; ++m) acc = fmaf(P.Ry[k * NN + m], tc[m], acc);
+      ph[k] = acc;
+    }
   }
-  if (active && !finite) atomicOr(status, SL_ST_NONFINITE);
+  float rm = 0.0f;                                // mass residual (same summation order everywhere)
+#pragma unroll
+  for (int q = 0; q < NN; ++q) rm += s_p[el][q];
+  if (P.bnd) {
+    const float* RxT = tab + P.o_RxT;
+    const float* RyT = tab + P.o_RyT;
+    float rx = 0.0f, vy = 0.0f, ty = 0.0f;
+#pragma unroll
+    for (int m = 0; m < NN; ++m) {
+      rx = fmaf(__ldg(RyT + m * NN + j), s_dx[el][m], rx);
+      vy = fmaf(__ldg(RxT + m * NN + j), s_v[el][m], vy);
+      ty = fmaf(P.liny[m], ph[m], ty);
+    }
+    s_r[el][j] = rx + (gx ? gval : 0.0f);
+    s_r[el][NN + j] = (vy + (gy ? gval : 0.0f)) - ty;
+  }
   __syncthreads();
-  // the TX elements of a tile row are consecutive in memory and in the staging rows
-  for (int idx = tid; idx < NE * ND; idx += NT) {
-    const int row = idx / (TX * ND), rem = idx - row * (TX * ND);
-    const int ex = ex0 + rem / ND, ey = ey0 + row;
-    if (ex < P.kx && ey < P.ky) {
-      const size_t g = ((size_t)ey * P.kx + ex0) * ND + rem;
-      const int sidx = (row * RW + P.xw) * ND + rem;
-      out[g] = s_hi[sidx];
-      out[P.plane + g] = s_lo[sidx];
+
+  // ---- fit: s = (C C^T)^+ r; thread j forms the face entries of row / column j
+  float sS = 0.0f, sN = 0.0f, sm = 0.0f;
+  if (P.bnd) {
+    const int mc = P.mc;
+    const float* G = tab + P.o_g;
+    float sW = 0.0f, sE = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 2 * NN; ++k) {
+      const float rk = s_r[el][k];
+      sW = fmaf(__ldg(G + (0 * mc + k) * NN + j), rk, sW);
+      sE = fmaf(__ldg(G + (1 * mc + k) * NN + j), rk, sE);
+      sS = fmaf(__ldg(G + (2 * mc + k) * NN + j), rk, sS);
+      sN = fmaf(__ldg(G + (3 * mc + k) * NN + j), rk, sN);
+      sm = fmaf(P.gm[k], rk, sm);
+    }
+    if (P.mass) {
+      sW = fmaf(__ldg(G + (0 * mc + 2 * NN) * NN + j), rm, sW);
+      sE = fmaf(__ldg(G + (1 * mc + 2 * NN) * NN + j), rm, sE);
+      sS = fmaf(__ldg(G + (2 * mc + 2 * NN) * NN + j), rm, sS);
+      sN = fmaf(__ldg(G + (3 * mc + 2 * NN) * NN + j), rm, sN);
+      sm = fmaf(P.gm[2 * NN], rm, sm);
+    }
+    s_sw[el][j] = sW;
+    s_se[el][j] = sE;
+    __syncthreads();
+  } else {
+    sm = P.gm[0] * rm;
+  }
+
+  // ---- phi_L = psihat + C^T s, column j; exact write-back into the own slot
+  {
+    const float l0j = __ldg(tab + P.o_l0 + j), l1j = __ldg(tab + P.o_l1 + j);
+    const float wj = __ldg(tab + P.o_w + j) * sm;
+    bool finite = true;
+#pragma unroll
+    for (int k = 0; k < NN; ++k) {
+      float acc = ph[k];
+      acc = fmaf(sS, P.l0[k], acc);
+      acc = fmaf(sN, P.l1[k], acc);
+      acc = fmaf(wj, P.w[k], acc);
+      if (P.bnd) {
+        acc = fmaf(s_sw[el][k], l0j, acc);
+        acc = fmaf(s_se[el][k], l1j, acc);
+      }
+      const float s = ref + acc;
+      const float bb = s - ref;
+      const float e = (ref - (s - bb)) + (acc - bb);
+      s_hi[so + k * NN + j] = s;
+      s_lo[so + k * NN + j] = e;
+      finite = finite && isfinite(s);
+    }
+    if (active && !finite) atomicOr(status, SL_ST_NONFINITE);
+  }
+  __syncthreads();
+
+  // ---- stores: the own elements of a tile row are one contiguous run; aligned vectors inside,
+  // single floats at its ends
+#pragma unroll 1
+  for (int r = 0; r < TY; ++r) {
+    const int eyr = ey0 + r;
+    if (eyr >= P.ky) break;
+    const int cnt = min(TX, P.kx - ex0);
+    const int64_t g0 = ((int64_t)eyr * P.kx + ex0) * ND, g1 = g0 + (int64_t)cnt * ND;
+    const int64_t A = floor4(g0 + 3), B = floor4(g1);
+    const int64_t a0 = s_a0[r];                   // global float G of this row is at r RS + (G - a0)
+    const float* rh = s_hi + r * RS;
+    const float* rl = s_lo + r * RS;
+    if (A <= B) {
+      const int nvec = (int)((B - A) >> 2);
+      for (int v = tid; v < nvec; v += NT) {
+        const int64_t G = A + 4 * (int64_t)v;
+        const int q = (int)(G - a0);
+        *reinterpret_cast<float4*>(out + G) = *reinterpret_cast<const float4*>(rh + q);
+        *reinterpret_cast<float4*>(out + P.plane + G) = *reinterpret_cast<const float4*>(rl + q);
+      }
+      if (tid < A - g0) {
+        const int q = (int)(g0 + tid - a0);
+        out[g0 + tid] = rh[q];
+        out[P.plane + g0 + tid] = rl[q];
+      }
+      if (tid < g1 - B) {
+        const int q = (int)(B + tid - a0);
+        out[B + tid] = rh[q];
+        out[P.plane + B + tid] = rl[q];
+      }
+    } else if (tid < g1 - g0) {
+      const int q = (int)(g0 + tid - a0);
+      out[g0 + tid] = rh[q];
+      out[P.plane + g0 + tid] = rl[q];
     }
   }
 }

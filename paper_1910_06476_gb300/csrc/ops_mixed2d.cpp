@@ -3,13 +3,15 @@
 // remap (eq. 5.4, separable: A_y (x) A_x), the face traces (eq. 2dx/2dy_bnd_interpolate), the
 // upwind values (eq. 4.12a), the mass target (eq. remap_mass with the RK quadrature of the face
 // flux) and the constrained fit (eq. matrix_a) reduce to a few small operators applied per
-// element in structured form:
+// element in structured form (psi: the element's n x n values, rows j = y index):
 //   psihat = R_y psi R_x^T                        (separable remap, R = A^{-1} of a uniform shift)
-//   trace of the x-upwind neighbour, row j   = sum_m R_y[j][m] sum_q psi_X[m][q] r_ox[q]
-//   trace of the y-upwind neighbour, col i   = sum_p R_x[i][p] sum_q r_oy[q] psi_Y[q][p]
-//   mass target (reference measure)          = K_self . psi + K_x . psi_X + K_y . psi_Y
-//   phi_L = psihat + C+_sub r, r = residuals of the inflow-face rows and the mass row (the
-//   outflow-face rows meet their targets exactly: they are this element's own traces).
+//   x inflow residual, row q = sum_m R_y[q][m] (psi_X[m][.] . r_ox - psi[m][.] . R_x^T l_in,x)
+//   y inflow residual, col i = sum_p R_x[i][p] (r_oy . psi_Y[.][p]) - l_in,y . psihat[.][i]
+//   mass residual            = K_s . psi + K_x . psi_X + K_y . psi_Y  (target minus mass of psihat)
+//   phi_L = psihat + C+ r = psihat + C^T s,  s = (C C^T)^+ r over the inflow-face and mass rows
+// (the outflow-face rows meet their targets exactly: they are this element's own traces).  C^T s
+// is separable: face rows are l0/l1 along one index and a unit vector along the other, the mass
+// row is w (x) w, so the correction costs five products per node.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -82,7 +84,7 @@ bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigne
   const FitOps& F = c->fit[cons & 3u][0];
   const int m = F.m;
   const bool bnd = cons & SL_C_BOUNDARY, mass = cons & SL_C_MASS;
-  std::vector<int> cols;                         // columns of C+ kept: inflow x rows, inflow y rows, mass
+  std::vector<int> cols;                         // residuals kept: inflow x rows, inflow y rows, mass
   if (bnd) {
     const int fx = xw ? 0 : 1, fy = ys ? 2 : 3;
     for (int q = 0; q < n; ++q) cols.push_back(fx * n + q);
@@ -90,7 +92,14 @@ bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigne
   }
   if (mass) cols.push_back(bnd ? 4 * n : 0);
   const int mc = (int)cols.size();
-  // float buffer layout
+  // (C C^T)^+ = (C+)^T C+, restricted to the kept columns: G[r][k]
+  std::vector<ld> G((size_t)m * mc, 0.0L);
+  for (int r = 0; r < m; ++r)
+    for (int k = 0; k < mc; ++k) {
+      ld acc = 0.0L;
+      for (int q = 0; q < nd; ++q) acc += (ld)F.Cpinv[q * m + r] * (ld)F.Cpinv[q * m + cols[k]];
+      G[(size_t)r * mc + k] = acc;
+    }
   P = Mixed2DConstParams{};
   P.n = n;
   P.kx = c->mesh.kx;
@@ -103,49 +112,71 @@ bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigne
   P.bnd = bnd ? 1 : 0;
   P.mass = mass ? 1 : 0;
   P.mc = mc;
-  P.flux_x = (float)(lam * std::fabs((ld)a) * hy);    // K_x applied to a constant c gives c |a| hy
-  P.flux_y = (float)(lam * std::fabs((ld)b) * hx);
+  for (int l = 0; l < n; ++l)
+    for (int q = 0; q < n; ++q) {
+      P.Rx[l * n + q] = (float)Rx[l * n + q];
+      P.Ry[l * n + q] = (float)Ry[l * n + q];
+    }
+  std::vector<ld> wxr(n, 0.0L), wyr(n, 0.0L);   // R_x^T w, R_y^T w: mass of psihat is wyr^T psi wxr
+  for (int p = 0; p < n; ++p) {
+    ld xi_in = 0.0L;
+    for (int l = 0; l < n; ++l) {
+      xi_in += Rx[l * n + p] * lin_x[l];
+      wxr[p] += Rx[l * n + p] * w[l];
+      wyr[p] += Ry[l * n + p] * w[l];
+    }
+    P.xix[p] = (float)xi_in;
+    P.rox[p] = (float)r_ox[p];
+    P.roy[p] = (float)r_oy[p];
+    P.liny[p] = (float)lin_y[p];
+    P.l0[p] = (float)l0[p];
+    P.l1[p] = (float)l1[p];
+    P.w[p] = (float)w[p];
+  }
+  if (mass) {
+    const int rm = bnd ? 4 * n : 0;
+    for (int k = 0; k < mc; ++k) P.gm[k] = (float)G[(size_t)rm * mc + k];
+  }
   buf.clear();
   auto put = [&](const std::vector<ld>& v) {
     size_t off = buf.size();
     for (ld x : v) buf.push_back((float)x);
     return (int)off;
   };
-  // threads read their own row of several tables: those are stored transposed ([col][row]) so
-  // that the n threads of an element read n consecutive floats
+  // tables a thread reads by its own row j are stored [other index][j], so that the n threads of
+  // an element read n consecutive floats
   auto transpose = [n](const std::vector<ld>& M) {
     std::vector<ld> T(M.size());
     for (int r = 0; r < n; ++r)
       for (int q = 0; q < n; ++q) T[q * n + r] = M[r * n + q];
     return T;
   };
-  P.o_Rx = put(Rx);
-  P.o_Ry = put(Ry);
-  P.o_RxT = put(transpose(Rx));
-  P.o_RyT = put(transpose(Ry));
-  P.o_linx = put(lin_x);
-  P.o_liny = put(lin_y);
-  P.o_rox = put(r_ox);
-  P.o_roy = put(r_oy);
-  std::vector<ld> Kself(nd), Kxl(nd), Kyl(nd), W2(nd);
+  // mass residual functionals (reference measure): own psi, x-neighbour psi_X (row j of each) and
+  // y-neighbour psi_Y (column j); the mass of psihat is folded into the own functional
+  std::vector<ld> Ks(nd), Kxl(nd), Kyl(nd);
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) {
       const int k = j * n + i;
-      W2[k] = w[j] * w[i];
-      Kself[k] = W2[k] - lam * (Kx[k] + Ky[k]);
+      Ks[k] = w[j] * w[i] - lam * (Kx[k] + Ky[k]) - wyr[j] * wxr[i];
       Kxl[k] = lam * Kx[k];
       Kyl[k] = lam * Ky[k];
     }
-  P.o_kself = put(transpose(Kself));
+  P.o_ks = put(transpose(Ks));
   P.o_kx = put(transpose(Kxl));
-  P.o_ky = put(transpose(Kyl));
-  P.o_w2 = put(transpose(W2));
-  // C+ restricted to the kept columns, as Cs[(l * mc + k) * n + j] for output node (j, l)
-  std::vector<ld> Cs(nd * std::max(mc, 1), 0.0L);
-  for (int j = 0; j < n; ++j)
-    for (int l = 0; l < n; ++l)
-      for (int k = 0; k < mc; ++k) Cs[(l * mc + k) * n + j] = (ld)F.Cpinv[(j * n + l) * m + cols[k]];
-  P.o_cp = put(Cs);
+  P.o_ky = put(Kyl);                             // column j of psi_Y: entry [m][j]
+  P.o_RxT = put(transpose(Rx));
+  P.o_RyT = put(transpose(Ry));
+  // face rows of G as Gt[(f * mc + k) * n + j] = G[f n + j][k], f = W, E, S, N
+  if (bnd) {
+    std::vector<ld> Gt((size_t)4 * mc * n);
+    for (int f = 0; f < 4; ++f)
+      for (int k = 0; k < mc; ++k)
+        for (int j = 0; j < n; ++j) Gt[((size_t)f * mc + k) * n + j] = G[(size_t)(f * n + j) * mc + k];
+    P.o_g = put(Gt);
+  }
+  P.o_l0 = put(l0);
+  P.o_l1 = put(l1);
+  P.o_w = put(w);
   buf.resize((buf.size() + 3) & ~size_t(3), 0.0f);
   return true;
 }

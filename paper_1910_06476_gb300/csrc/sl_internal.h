@@ -102,14 +102,23 @@ void launch_step2d_mixed(int n, const StepParams& p, const Mixed2DExtra& x, cons
                          unsigned* status, cudaStream_t s);
 inline int64_t work2m_floats(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 16 + 4); }
 
-// Parameters of the 2D shared-operator kernel (uniform mesh, constant velocity); the operators
-// live in a float table at the given offsets
+// Parameters of the 2D shared-operator kernel (uniform mesh, constant velocity).  Operators that
+// every thread applies with the same entry live here (the kernel reads them from the parameter
+// bank); operators read per row live in a float table at the given offsets.
 struct Mixed2DConstParams {
   int n, kx, ky, xw, ys, per_x, per_y, bnd, mass, mc;
   double ghost;
-  float flux_x, flux_y;
   int64_t plane;
-  int o_Rx, o_Ry, o_RxT, o_RyT, o_linx, o_liny, o_rox, o_roy, o_kself, o_kx, o_ky, o_w2, o_cp;
+  float Rx[NMAX * NMAX], Ry[NMAX * NMAX];   // remap matrices [l][p]: l_p(xi_l - shift)
+  float xix[NMAX];                          // R_x^T l_in,x: own inflow x-trace functional of a row
+  float rox[NMAX], roy[NMAX];               // R^T l_out: upwind neighbour outflow-trace functionals
+  float liny[NMAX];                         // l_in,y: inflow y-trace of a remapped column
+  float l0[NMAX], l1[NMAX], w[NMAX];        // basis at 0 and 1, quadrature weights
+  float gm[2 * NMAX + 1];                   // mass row of (C C^T)^+ over the kept residuals
+  int o_ks, o_kx, o_ky;                     // mass-target functionals (own, x-, y-neighbour)
+  int o_RxT, o_RyT;                         // transposed remap matrices
+  int o_g;                                  // face rows of (C C^T)^+ over the kept residuals
+  int o_l0, o_l1, o_w;                      // l0, l1, w again, read per thread
 };
 bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigned cons, int rk,
                          std::vector<float>& buf, Mixed2DConstParams& P, std::string& err);
