@@ -130,6 +130,12 @@ typedef struct {
 
 /* Create a context for one mesh.  n = nodes per direction (polynomial degree n - 1),
  * 2 <= n <= 17 (ignored when mesh->order is given, whose entries must lie in [2, 17]).
+ * mesh->order makes a p-adaptive 2D mesh (1D: SL_EUNSUPPORTED): element (ex, ey) has
+ * order[ey*kx + ex] nodes per direction, its state is stored at the CSR offset described
+ * above, and a face between elements of different node counts is handled as follows: the
+ * upwind value at a face point is the neighbour's remapped polynomial evaluated there, and the
+ * mass/energy flux through the face is integrated once with the Gauss rule of the side with
+ * more nodes, so both elements see the same flux and global mass telescopes.
  * cuda_stream: a cudaStream_t (0 = legacy default stream).  Precomputes, in host double
  * and long double arithmetic, the nodes, weights, face basis values and fit operators
  * (Sec. 3, eq. 3.5, quad, matrix_a) and uploads them.  On success *out owns device memory
@@ -155,6 +161,25 @@ sl_status sl_step(sl_ctx* ctx, const void* phi_in, void* phi_out, const sl_veloc
 sl_status sl_run_host(sl_ctx* ctx, const double* host_in, double* host_out, const sl_velocity* vel,
                       double t0, double dt, int nsteps, const sl_options* opt);
 
+/* Batches of independent 2D problems advanced by the same launches (one pair of kernel launches
+ * per node count present, whatever the number of problems).  sl_batch_create builds a batch
+ * context from nprob problem contexts (host array, 1 <= nprob <= 65535; each made by sl_init,
+ * all with the same basis and precision, uniform or p-adaptive).  The batch state is the
+ * problems' states concatenated in problem order, as one state of sl_state_size values in the
+ * context's state format: problem p's node values start at value offset sl_batch_offset(batch,
+ * p) (sl_batch_offset(batch, nprob) is the total; -1 on a bad argument).  For SL_MIXED the
+ * planes span the whole batch, so a problem's part is reached through sl_unpack.  The batch
+ * context works with every entry point taking a context; it keeps copies of the problems'
+ * meshes (the problem contexts may be freed), uses the stream of probs[0], and is released with
+ * sl_free.  sl_step advances every problem with the same t and dt; sl_batch_step takes host
+ * arrays of nprob times and steps (each checked against its problem's element size, SL_ECFL).
+ * sl_max_dt returns the smallest limit over the problems.  sl_mass and sl_energy sum over all
+ * problems. */
+sl_status sl_batch_create(int nprob, sl_ctx* const* probs, sl_ctx** batch);
+sl_status sl_batch_step(sl_ctx* batch, const void* phi_in, void* phi_out, const sl_velocity* vel,
+                        const double* t, const double* dt, const sl_options* opt);
+int64_t sl_batch_offset(const sl_ctx* batch, int p);
+
 /* Convert sl_state_size doubles (device) into the context's state format (device, sl_state_bytes
  * bytes), and back.  For SL_FP64 these are plain copies.  Enqueued on the context's stream. */
 sl_status sl_pack(sl_ctx* ctx, const double* src, void* dst);
@@ -177,7 +202,8 @@ int64_t sl_state_size(const sl_ctx* ctx);
 int64_t sl_state_bytes(const sl_ctx* ctx);
 
 /* Physical node coordinates in state layout, written to host arrays of sl_state_size
- * doubles (y may be null in 1D), for setting up initial data. */
+ * doubles (y may be null in 1D), for setting up initial data (a batch: every problem's nodes in
+ * its own box). */
 sl_status sl_node_coords(const sl_ctx* ctx, double* x, double* y);
 
 /* Quadrature nodes and weights on [0, 1] of the context's basis for n nodes (host arrays). */

@@ -26,7 +26,7 @@ ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV = 1, 2, 4
 
 EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
            "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",
-           "sl_integral_noalloc", "sl_last_error"]
+           "sl_integral_noalloc", "sl_batch_create", "sl_batch_step", "sl_batch_offset", "sl_last_error"]
 
 
 class SlMesh(C.Structure):
@@ -76,10 +76,14 @@ def load_library(path=LIB_PATH):
     lib.sl_node_coords.argtypes = [P, P, P]
     lib.sl_nodes_weights.argtypes = [P, C.c_int, P, P]
     lib.sl_integral_noalloc.argtypes = [P, C.c_int64, C.c_int, C.c_int, P, C.c_int, C.c_double, P, P]
+    lib.sl_batch_create.argtypes = [C.c_int, C.POINTER(P), C.POINTER(P)]
+    lib.sl_batch_step.argtypes = [P, P, P, C.POINTER(SlVelocity), P, P, C.POINTER(SlOptions)]
+    lib.sl_batch_offset.argtypes = [P, C.c_int]
+    lib.sl_batch_offset.restype = C.c_int64
     lib.sl_last_error.argtypes = [P]
     lib.sl_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("sl_free", "sl_state_size", "sl_state_bytes", "sl_last_error"):
+        if name not in ("sl_free", "sl_state_size", "sl_state_bytes", "sl_batch_offset", "sl_last_error"):
             getattr(lib, name).restype = C.c_int
     return lib
 
@@ -117,7 +121,9 @@ class Context:
     """One mesh on one GPU stream (sl_init ... sl_free)."""
 
     def __init__(self, dim, kx, ky, box, n, basis=GAUSS_LEGENDRE, precision=FP64, bc=(0, 0, 0, 0),
-                 ghost=0.0, stream=None):
+                 ghost=0.0, stream=None, orders=None):
+        """orders: optional (ky, kx) integer array of per-element node counts (p-adaptive 2D
+        mesh); the state is then flat, element by element (row-major), n_e^2 values each."""
         import torch
         self._lib = lib()
         m = SlMesh()
@@ -126,7 +132,12 @@ class Context:
         for i in range(4):
             m.bc[i] = int(bc[i])
         m.ghost = float(ghost)
-        m.order = C.POINTER(C.c_int32)()
+        self.orders = None
+        if orders is not None:
+            self.orders = np.ascontiguousarray(np.asarray(orders, dtype=np.int32).reshape(ky, kx))
+            m.order = self.orders.ctypes.data_as(C.POINTER(C.c_int32))
+        else:
+            m.order = C.POINTER(C.c_int32)()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         st = self._lib.sl_init(C.byref(m), int(n), int(basis), int(precision),
@@ -135,9 +146,13 @@ class Context:
             raise SlError(st, self._lib.sl_last_error(None).decode())
         self._h = h
         self.dim, self.kx, self.ky, self.n, self.precision = dim, kx, ky, n, precision
+        self._setup(h, precision)
+        self.shape = (self.size,) if orders is not None else (kx, n) if dim == 1 else (ky, kx, n, n)
+
+    def _setup(self, h, precision):
+        import torch
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.size = int(self._lib.sl_state_size(h))
-        self.shape = (kx, n) if dim == 1 else (ky, kx, n, n)
         # number of state elements of self.dtype in one state buffer (two float planes when mixed)
         self.numel = int(self._lib.sl_state_bytes(h)) // (8 if precision == FP64 else 4)
 
@@ -229,3 +244,37 @@ class Context:
         self._check(self._lib.sl_nodes_weights(self._h, int(n), xi.ctypes.data_as(C.c_void_p),
                                                w.ctypes.data_as(C.c_void_p)))
         return xi, w
+
+
+class Batch(Context):
+    """Independent 2D problems advanced together (sl_batch_create): the batch state is the
+    problems' states concatenated; problem p's values start at offset(p)."""
+
+    def __init__(self, problems):
+        self._lib = lib()
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        h = C.c_void_p()
+        st = self._lib.sl_batch_create(len(self.problems), arr, C.byref(h))
+        if st != SL_OK:
+            raise SlError(st, self._lib.sl_last_error(None).decode())
+        self._h = h
+        p0 = self.problems[0]
+        self.dim, self.n, self.precision, self.stream = 2, None, p0.precision, p0.stream
+        self._setup(h, p0.precision)
+        self.shape = (self.size,)
+
+    def offset(self, p):
+        return int(self._lib.sl_batch_offset(self._h, int(p)))
+
+    def batch_step(self, phi_in, phi_out, vel, t, dt, opts):
+        """t, dt: one time and step per problem."""
+        self._state(phi_in, "phi_in")
+        self._state(phi_out, "phi_out")
+        ta = np.ascontiguousarray(np.asarray(t, dtype=np.float64))
+        da = np.ascontiguousarray(np.asarray(dt, dtype=np.float64))
+        if ta.size != len(self.problems) or da.size != len(self.problems):
+            raise ValueError("one t and one dt per problem")
+        self._check(self._lib.sl_batch_step(self._h, _ptr(phi_in), _ptr(phi_out), C.byref(vel),
+                                            ta.ctypes.data_as(C.c_void_p), da.ctypes.data_as(C.c_void_p),
+                                            C.byref(opts)))

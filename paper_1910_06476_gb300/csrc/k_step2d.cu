@@ -4,31 +4,29 @@
 namespace sl {
 namespace k2d {
 template <int NN>
-void launch_n(const StepParams& p, const Tables1D& tb, const double* in, double* out, Work2D w, unsigned* st,
-              cudaStream_t s);
+void launch_n(int phase, const StepParams& p, const Tables1D& tb, const Map2D& m, int64_t count, const double* in,
+              double* out, const Work2D& w, unsigned* st, cudaStream_t s);
 }
 
-void launch_step2d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in, double* out, double* work,
-                       unsigned* status, cudaStream_t s) {
-  const int64_t nel = (int64_t)p.kx * p.ky;
-  k2d::Work2D w{work, work + nel * n * n, work + nel * (n * n + 4 * n)};
+void launch_step2d_f64(int phase, int n, const StepParams& p, const Tables1D& tb, const Map2D& m, int64_t count,
+                       const double* in, double* out, const Work2D& w, unsigned* status, cudaStream_t s) {
   switch (n) {
-    case 2: k2d::launch_n<2>(p, tb, in, out, w, status, s); break;
-    case 3: k2d::launch_n<3>(p, tb, in, out, w, status, s); break;
-    case 4: k2d::launch_n<4>(p, tb, in, out, w, status, s); break;
-    case 5: k2d::launch_n<5>(p, tb, in, out, w, status, s); break;
-    case 6: k2d::launch_n<6>(p, tb, in, out, w, status, s); break;
-    case 7: k2d::launch_n<7>(p, tb, in, out, w, status, s); break;
-    case 8: k2d::launch_n<8>(p, tb, in, out, w, status, s); break;
-    case 9: k2d::launch_n<9>(p, tb, in, out, w, status, s); break;
-    case 10: k2d::launch_n<10>(p, tb, in, out, w, status, s); break;
-    case 11: k2d::launch_n<11>(p, tb, in, out, w, status, s); break;
-    case 12: k2d::launch_n<12>(p, tb, in, out, w, status, s); break;
-    case 13: k2d::launch_n<13>(p, tb, in, out, w, status, s); break;
-    case 14: k2d::launch_n<14>(p, tb, in, out, w, status, s); break;
-    case 15: k2d::launch_n<15>(p, tb, in, out, w, status, s); break;
-    case 16: k2d::launch_n<16>(p, tb, in, out, w, status, s); break;
-    case 17: k2d::launch_n<17>(p, tb, in, out, w, status, s); break;
+    case 2: k2d::launch_n<2>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 3: k2d::launch_n<3>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 4: k2d::launch_n<4>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 5: k2d::launch_n<5>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 6: k2d::launch_n<6>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 7: k2d::launch_n<7>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 8: k2d::launch_n<8>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 9: k2d::launch_n<9>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 10: k2d::launch_n<10>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 11: k2d::launch_n<11>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 12: k2d::launch_n<12>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 13: k2d::launch_n<13>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 14: k2d::launch_n<14>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 15: k2d::launch_n<15>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 16: k2d::launch_n<16>(phase, p, tb, m, count, in, out, w, status, s); break;
+    case 17: k2d::launch_n<17>(phase, p, tb, m, count, in, out, w, status, s); break;
     default: break;
   }
 }

@@ -3,10 +3,15 @@
 
 namespace sl {
 namespace k2d {
-template void launch_n<2>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<3>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<4>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<5>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<6>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
+template void launch_n<2>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<3>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<4>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<5>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<6>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
 }  // namespace k2d
 }  // namespace sl

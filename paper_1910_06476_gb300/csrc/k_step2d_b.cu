@@ -3,9 +3,13 @@
 
 namespace sl {
 namespace k2d {
-template void launch_n<7>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<8>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<9>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<10>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
+template void launch_n<7>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<8>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<9>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<10>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
 }  // namespace k2d
 }  // namespace sl

@@ -3,8 +3,11 @@
 
 namespace sl {
 namespace k2d {
-template void launch_n<11>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<12>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<13>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
+template void launch_n<11>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<12>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<13>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
 }  // namespace k2d
 }  // namespace sl

@@ -3,9 +3,13 @@
 
 namespace sl {
 namespace k2d {
-template void launch_n<14>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<15>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<16>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
-template void launch_n<17>(const StepParams&, const Tables1D&, const double*, double*, Work2D, unsigned*, cudaStream_t);
+template void launch_n<14>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<15>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<16>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
+template void launch_n<17>(int, const StepParams&, const Tables1D&, const Map2D&, int64_t, const double*, double*,
+                            const Work2D&, unsigned*, cudaStream_t);
 }  // namespace k2d
 }  // namespace sl

@@ -18,7 +18,7 @@
 // phihat <- phihat + M^{-1} (phi* - H phihat), with M = A_y (x) A_x the exact matrix of a uniform
 // shift by the element's mean particle displacement, whose inverse is the 1D remap R_y (x) R_x.
 // H phihat costs n^2 per particle (the advected basis values are kept in registers).
-#include "sl_internal.h"
+#include "k_map2d.cuh"
 
 namespace sl {
 namespace k2d {
@@ -142,12 +142,6 @@ struct Shape {
   static constexpr int NT = ((ND > 4 * NN ? ND : 4 * NN) + 31) / 32 * 32;   // threads per CTA
 };
 
-struct Work2D {            // workspace between the two phases
-  double* phihat;          // [nel][n^2]
-  double* traces;          // [nel][4][n]   faces W, E, S, N at the tangential nodes
-  double* fluxes;          // [nel][4][2]   outflow (mass, energy) flux per face over the step
-};
-
 __device__ __forceinline__ int nb_index(const StepParams& P, int ex, int ey, int face, bool& wrapped) {
   int jx = ex + (face == 0 ? -1 : face == 1 ? 1 : 0);
   int jy = ey + (face == 2 ? -1 : face == 3 ? 1 : 0);
@@ -161,17 +155,19 @@ __device__ __forceinline__ int nb_index(const StepParams& P, int ex, int ey, int
 }
 
 template <int NN>
-__global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, Tables1D tb, const double* __restrict__ in,
-                                                     Work2D W, unsigned* status) {
+__global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb, Map2D M,
+                                                     const double* __restrict__ in, Work2D W, unsigned* status) {
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
   __shared__ double s_xi[NN], s_lam[NN], s_w[NN], s_l0[NN], s_l1[NN];
   __shared__ double s_phi[ND], s_ph[ND], s_t[ND], s_r[ND];
   __shared__ double s_Rx[ND], s_Ry[ND];
   __shared__ double s_red[NT / 32];
-  __shared__ double s_face[4][NN][2];
+  __shared__ double s_face[4][NMAX][2];
+  __shared__ int s_nq[4];
   const int tid = threadIdx.x;
-  const int e = blockIdx.x;
-  const int ex = e % P.kx, ey = e / P.kx;
+  StepParams P = P0;
+  const Elem E = elem_of<NN>(P, M);
+  const int ex = E.ex, ey = E.ey;
   const double hx = P.hx, hy = P.hy;
   const double x0 = P.x0 + ex * hx, y0 = P.y0 + ey * hy;
   if (tid < NN) {
@@ -180,7 +176,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, Tables1D tb,
   }
   const bool part = tid < ND;
   const int i = tid % NN, j = tid / NN;
-  if (part) s_phi[tid] = in[(size_t)e * ND + tid];
+  if (part) s_phi[tid] = in[E.base + tid];
   __syncthreads();
 
   // (a)-(b) seed and advect the particle of node (i, j)
@@ -250,7 +246,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, Tables1D tb,
     precond_add(false);
   }
   if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);
-  if (part) W.phihat[(size_t)e * ND + tid] = s_ph[tid];
+  if (part) W.phihat[E.base + tid] = s_ph[tid];
 
   // traces of phihat at the four faces, thread (face, q)
   if (tid < 4 * NN) {
@@ -259,17 +255,28 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, Tables1D tb,
     double acc = 0.0;
 #pragma unroll
     for (int k = 0; k < NN; ++k) acc += (f < 2 ? s_ph[q * NN + k] : s_ph[k * NN + q]) * L[k];
-    W.traces[(size_t)e * 4 * NN + tid] = acc;
+    W.traces[E.g * M.tstride + tid] = acc;
   }
-  // outflow fluxes: for each face point and RK stage where u.n_out > TIE, phi^n at the foot
+  // outflow fluxes: for each face point and RK stage where u.n_out > TIE, phi^n at the foot.
+  // A face shared with a neighbour of another node count takes the rule of the finer side, so
+  // that both elements integrate the same points (the flux telescopes).
   if (P.cons & (SL_C_MASS | SL_C_ENERGY)) {
-    double fm = 0.0, fe = 0.0;
-    if (tid < 4 * NN) {
-      const int f = tid / NN, q = tid % NN;
-      const double xf = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
-      const double yf = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
+    if (tid < 4) {
+      bool wr;
+      const int nb = nb_index(P, ex, ey, tid, wr);
+      s_nq[tid] = nb < 0 ? NN : max(NN, order_of<NN>(M, E.gb + nb));
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 4 * NMAX; idx += NT) {
+      const int f = idx / NMAX, q = idx % NMAX;
+      const int nq = s_nq[f];
+      if (q >= nq) continue;
+      const double* rule = tb.rules + (size_t)nq * 3 * NMAX;
+      double fm = 0.0, fe = 0.0;
+      const double xf = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * rule[q];
+      const double yf = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * rule[q];
       const double nx = f == 0 ? -1.0 : f == 1 ? 1.0 : 0.0, ny = f == 2 ? -1.0 : f == 3 ? 1.0 : 0.0;
-      const double Wq = (f < 2 ? hy : hx) * s_w[q];
+      const double Wq = (f < 2 ? hy : hx) * rule[2 * NMAX + q];
       const int S = c_rk_s[P.rk];
       for (int s = 0; s < S; ++s) {
         const double cs = c_rk_c[P.rk][s];
@@ -303,15 +310,16 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, Tables1D tb,
     if (tid < 8) {                           // per face, sum over the points in index order
       const int f = tid >> 1, k = tid & 1;
       double acc = 0.0;
-      for (int q = 0; q < NN; ++q) acc += s_face[f][q][k];
-      W.fluxes[(size_t)e * 8 + tid] = acc;
+      for (int q = 0; q < s_nq[f]; ++q) acc += s_face[f][q][k];
+      W.fluxes[E.g * 8 + tid] = acc;
     }
   }
 }
 
 template <int NN>
-__global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, Tables1D tb, const double* __restrict__ in,
-                                                     Work2D W, double* __restrict__ out, unsigned* status) {
+__global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, Tables1D tb, Map2D M,
+                                                     const double* __restrict__ in, Work2D W, double* __restrict__ out,
+                                                     unsigned* status) {
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
   constexpr int MMAX = 4 * NN + 1;
   __shared__ double s_xi[NN], s_w[NN], s_l0[NN], s_l1[NN];
@@ -319,8 +327,9 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, Tables1D tb,
   __shared__ double s_r[MMAX], s_d[MMAX], s_ca[MMAX];
   __shared__ double s_red[NT / 32];
   const int tid = threadIdx.x;
-  const int e = blockIdx.x;
-  const int ex = e % P.kx, ey = e / P.kx;
+  StepParams P = P0;
+  const Elem E = elem_of<NN>(P, M);
+  const int ex = E.ex, ey = E.ey;
   const double hx = P.hx, hy = P.hy;
   const double x0 = P.x0 + ex * hx, y0 = P.y0 + ey * hy;
   const double tn1 = P.t + P.dt;
@@ -329,8 +338,8 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, Tables1D tb,
   const int i = tid % NN, j = tid / NN;
   double phn = 0.0, ph = 0.0;
   if (part) {
-    phn = in[(size_t)e * ND + tid];
-    ph = W.phihat[(size_t)e * ND + tid];
+    phn = in[E.base + tid];
+    ph = W.phihat[E.base + tid];
     s_ph[tid] = ph;
   }
   __syncthreads();
@@ -343,8 +352,13 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, Tables1D tb,
     bool wr;
     const int nb = nb_index(P, ex, ey, f, wr);
     const int fo = f ^ 1;                    // opposite face of the neighbour
-    const double own = W.traces[(size_t)e * 4 * NN + tid];
-    const double other = nb >= 0 ? W.traces[(size_t)nb * 4 * NN + fo * NN + q] : P.ghost;
+    const double own = W.traces[E.g * M.tstride + tid];
+    double other = P.ghost;
+    if (nb >= 0) {                           // the neighbour's trace at this element's face points
+      const int nn = order_of<NN>(M, E.gb + nb);
+      const double* tr = W.traces + (E.gb + nb) * M.tstride + fo * nn;
+      other = nn == NN ? tr[q] : interp_rule(tb.rules, nn, tr, s_xi[q]);
+    }
     const double xf = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
     const double yf = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
     double u, v;
@@ -366,11 +380,11 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, Tables1D tb,
       for (int f = 0; f < 4; ++f) {
         bool wr;
         const int nb = nb_index(P, ex, ey, f, wr);
-        netm += W.fluxes[(size_t)e * 8 + 2 * f];
-        nete += W.fluxes[(size_t)e * 8 + 2 * f + 1];
+        netm += W.fluxes[E.g * 8 + 2 * f];
+        nete += W.fluxes[E.g * 8 + 2 * f + 1];
         if (nb >= 0) {
-          netm -= W.fluxes[(size_t)nb * 8 + 2 * (f ^ 1)];
-          nete -= W.fluxes[(size_t)nb * 8 + 2 * (f ^ 1) + 1];
+          netm -= W.fluxes[(E.gb + nb) * 8 + 2 * (f ^ 1)];
+          nete -= W.fluxes[(E.gb + nb) * 8 + 2 * (f ^ 1) + 1];
         } else {                              // inflow from the ghost value at a domain face
           for (int q = 0; q < NN; ++q) {
             const double xf = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
@@ -496,18 +510,18 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, Tables1D tb,
     }
   }
   if (part) {
-    out[(size_t)e * ND + tid] = cur;
+    out[E.base + tid] = cur;
     if (!isfinite(cur)) atomicOr(status, SL_ST_NONFINITE);
   }
   if (!ok && tid == 0) atomicOr(status, SL_ST_PICARD_NOCONV);
 }
 
 template <int NN>
-void launch_n(const StepParams& p, const Tables1D& tb, const double* in, double* out, Work2D w, unsigned* st,
-              cudaStream_t s) {
-  const int nel = p.kx * p.ky;
-  k_p1<NN><<<nel, Shape<NN>::NT, 0, s>>>(p, tb, in, w, st);
-  k_p2<NN><<<nel, Shape<NN>::NT, 0, s>>>(p, tb, in, w, out, st);
+void launch_n(int phase, const StepParams& p, const Tables1D& tb, const Map2D& m, int64_t count, const double* in,
+              double* out, const Work2D& w, unsigned* st, cudaStream_t s) {
+  if (count <= 0) return;
+  if (phase == 1) k_p1<NN><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, tb, m, in, w, st);
+  else k_p2<NN><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, tb, m, in, w, out, st);
 }
 
 }  // namespace k2d

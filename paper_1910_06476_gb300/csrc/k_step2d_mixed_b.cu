@@ -3,9 +3,13 @@
 
 namespace sl {
 namespace k2m {
-template void launch_n<9>(const StepParams&, const Mixed2DExtra&, const float*, float*, Work2M, unsigned*, cudaStream_t);
-template void launch_n<10>(const StepParams&, const Mixed2DExtra&, const float*, float*, Work2M, unsigned*, cudaStream_t);
-template void launch_n<11>(const StepParams&, const Mixed2DExtra&, const float*, float*, Work2M, unsigned*, cudaStream_t);
-template void launch_n<12>(const StepParams&, const Mixed2DExtra&, const float*, float*, Work2M, unsigned*, cudaStream_t);
+template void launch_n<9>(int, const StepParams&, const Mixed2DExtra&, const Map2D&, int64_t, const float*, float*,
+                            const Work2M&, unsigned*, cudaStream_t);
+template void launch_n<10>(int, const StepParams&, const Mixed2DExtra&, const Map2D&, int64_t, const float*, float*,
+                            const Work2M&, unsigned*, cudaStream_t);
+template void launch_n<11>(int, const StepParams&, const Mixed2DExtra&, const Map2D&, int64_t, const float*, float*,
+                            const Work2M&, unsigned*, cudaStream_t);
+template void launch_n<12>(int, const StepParams&, const Mixed2DExtra&, const Map2D&, int64_t, const float*, float*,
+                            const Work2M&, unsigned*, cudaStream_t);
 }  // namespace k2m
 }  // namespace sl

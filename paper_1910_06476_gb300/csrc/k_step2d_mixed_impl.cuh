@@ -8,12 +8,19 @@
 //              U_out, U_in : RK/Gauss quadrature of u.n_out split by its sign,
 //              Psi, Psi2   : the same of u.n psi and u.n psi^2 at the feet of the outflow points;
 //   phase 2: interface values, mass and energy targets, constrained fit, energy iteration.
+// Without the energy row the element reference is linear, L = r0 + gx (xi - 1/2) + gy (eta - 1/2)
+// (from the corner values; evaluated in double wherever a node value is formed), and psi = phi - L
+// is what the float arithmetic carries: for resolved data it is smaller than phi - r0 by about the
+// element width over the data's length scale, and so is every rounding error of the remap, the
+// traces and the fit.  Particles keep phi (divergence-free velocity), so the collocation data for
+// psihat = phihat - L is psi_p - grad L . d_p (d_p the particle's displacement).  With the energy
+// row the reference is the constant r0 (gx = gy = 0).
 // Everything a target needs is assembled from increments: the net mass flux of element e is
 //   ref_e (U_out + U_in)  +  sum_f (ref_nb - ref_e) U_in,f  +  sum_f (Psi_out,f - Psi'_f),
 // Psi'_f being the neighbour's outflow flux through the shared face, so float rounding scales
 // with the variation of the data instead of |phi|.  The result is written back exactly as
 // ref + psi (TwoSum).
-#include "sl_internal.h"
+#include "k_map2d.cuh"
 
 namespace sl {
 namespace k2m {
@@ -138,14 +145,20 @@ struct Shape {
   static constexpr int NT = ((ND > 4 * NN ? ND : 4 * NN) + 31) / 32 * 32;
 };
 
-// workspace (floats) per element: psihat [n^2], traces [4n], face sums [4][4] (U_out, U_in, Psi,
-// Psi2), element sums [4] (ref, sum w psi, sum w psi^2, unused)
-struct Work2M {
-  float* psihat;
-  float* traces;
-  float* faces;
-  float* elem;
-};
+// per-problem float parameters of a batch element (the FP64 geometry is already in P)
+__device__ __forceinline__ void batch_extra(const StepParams& P, const Map2D& M, Mixed2DExtra& X) {
+  if (!M.geo) return;
+  X.hx = (float)P.hx;
+  X.hy = (float)P.hy;
+  X.ihx = (float)(1.0 / P.hx);
+  X.ihy = (float)(1.0 / P.hy);
+  X.dt = (float)P.dt;
+  X.dt_area = (float)(P.dt / (P.hx * P.hy));
+  if (X.Tper != 0.0) {
+    X.tT = (float)(P.t / X.Tper);
+    X.dtT = (float)(P.dt / X.Tper);
+  }
+}
 
 __device__ __forceinline__ int nb_index(const StepParams& P, int ex, int ey, int face) {
   int jx = ex + (face == 0 ? -1 : face == 1 ? 1 : 0);
@@ -157,17 +170,27 @@ __device__ __forceinline__ int nb_index(const StepParams& P, int ex, int ey, int
   return jy * P.kx + jx;
 }
 
+// element reference L = r0 + gx (xi - 1/2) + gy (eta - 1/2) in double
+__device__ __forceinline__ double lref(float r0, float gx, float gy, double xi, double eta) {
+  return (double)r0 + (double)gx * (xi - 0.5) + (double)gy * (eta - 0.5);
+}
+
 template <int NN>
-__global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid_constant__ Mixed2DExtra X,
-                                                     const float* __restrict__ in, Work2M W, unsigned* status) {
+__global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, const __grid_constant__ Mixed2DExtra X0,
+                                                     Map2D M, const float* __restrict__ in, Work2M W,
+                                                     unsigned* status) {
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
   __shared__ float s_xi[NN], s_lam[NN], s_w[NN], s_l0[NN], s_l1[NN];
   __shared__ float s_psi[ND], s_ph[ND], s_t[ND], s_r[ND], s_Rx[ND], s_Ry[ND];
   __shared__ float s_red[NT / 32];
-  __shared__ float s_face[4][NN][4];
+  __shared__ float s_face[4][NMAX][4];
+  __shared__ int s_nq[4];
   const int tid = threadIdx.x;
-  const int e = blockIdx.x;
-  const int ex = e % P.kx, ey = e / P.kx;
+  StepParams P = P0;
+  const Elem E = elem_of<NN>(P, M);
+  Mixed2DExtra X = X0;
+  batch_extra(P, M, X);
+  const int ex = E.ex, ey = E.ey;
   const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
   if (tid < NN) {
     s_xi[tid] = X.xi[tid]; s_lam[tid] = X.lam[tid]; s_w[tid] = X.w[tid];
@@ -175,18 +198,29 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
   }
   const bool part = tid < ND;
   const int i = tid % NN, j = tid / NN;
-  const float ref = in[(size_t)e * ND];
-  if (part) s_psi[tid] = (in[(size_t)e * ND + tid] - ref) + in[X.plane + (size_t)e * ND + tid];
+  // element reference: linear from the four corner values, or the first node value
+  const float c00 = in[E.base], c01 = in[E.base + NN - 1], c10 = in[E.base + (NN - 1) * NN], c11 = in[E.base + ND - 1];
+  float ref = c00, gx = 0.0f, gy = 0.0f;
+  if (X.linref) {
+    const float span = (float)(0.5 / (X.xid[NN - 1] - X.xid[0]));
+    ref = 0.25f * ((c00 + c01) + (c10 + c11));
+    gx = ((c01 + c11) - (c00 + c10)) * span;
+    gy = ((c10 + c11) - (c00 + c01)) * span;
+  }
+  if (part)
+    s_psi[tid] = (float)(((double)in[E.base + tid] + (double)in[X.plane + E.base + tid]) -
+                         lref(ref, gx, gy, X.xid[i], X.xid[j]));
   __syncthreads();
 
   // advect the particle of node (i, j) in reference coordinates
-  float Lx[NN], Ly[NN], ps = 0.0f, dxs = 0.0f, dys = 0.0f;
+  float Lx[NN], Ly[NN], ps = 0.0f, pn = 0.0f, dxs = 0.0f, dys = 0.0f;
   if (part) {
     float ddx = 0.0f, ddy = 0.0f;
     rk_disp(P, X, x0, y0, s_xi[i], s_xi[j], ddx, ddy, X.tT, X.dt, X.dtT);
     basis_at<NN>(s_xi, s_lam, s_xi[i], ddx, Lx);
     basis_at<NN>(s_xi, s_lam, s_xi[j], ddy, Ly);
-    ps = s_psi[tid];
+    pn = s_psi[tid];
+    ps = pn - fmaf(gx, ddx, gy * ddy);       // collocation data of phihat - L
     dxs = ddx;
     dys = ddy;
   }
@@ -259,16 +293,17 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
     precond_add(false);
   }
   if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);
-  if (part) W.psihat[(size_t)e * ND + tid] = s_ph[tid];
+  if (part) W.psihat[E.base + tid] = s_ph[tid];
   // element sums of psi^n (reference measure)
   const float w2 = part ? s_w[i] * s_w[j] : 0.0f;
-  const float m1 = block_sum<NT>(w2 * ps, s_red);
-  const float m2 = block_sum<NT>(w2 * ps * ps, s_red);
+  const float m1 = block_sum<NT>(w2 * pn, s_red);
+  const float m2 = block_sum<NT>(w2 * pn * pn, s_red);
   if (tid == 0) {
-    W.elem[(size_t)e * 4 + 0] = ref;
-    W.elem[(size_t)e * 4 + 1] = m1;
-    W.elem[(size_t)e * 4 + 2] = m2;
-    W.elem[(size_t)e * 4 + 3] = 0.0f;
+    W.elem[E.g * 8 + 0] = ref;
+    W.elem[E.g * 8 + 1] = gx;
+    W.elem[E.g * 8 + 2] = gy;
+    W.elem[E.g * 8 + 3] = m1;
+    W.elem[E.g * 8 + 4] = m2;
   }
   // traces of psihat (relative to ref)
   if (tid < 4 * NN) {
@@ -277,17 +312,26 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
     float acc = 0.0f;
 #pragma unroll
     for (int k = 0; k < NN; ++k) acc = fmaf(f < 2 ? s_ph[q * NN + k] : s_ph[k * NN + q], L[k], acc);
-    W.traces[(size_t)e * 4 * NN + tid] = acc;
+    W.traces[E.g * M.tstride + tid] = acc;
   }
-  // face sums over the step
+  // face sums over the step; a face shared with a neighbour of another node count takes the rule
+  // of the finer side, so that both elements integrate the same points
   if (P.cons & (SL_C_MASS | SL_C_ENERGY)) {
-    if (tid < 4 * NN) {
-      const int f = tid / NN, q = tid % NN;
-      const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : s_xi[q];
-      const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : s_xi[q];
+    if (tid < 4) {
+      const int nb = nb_index(P, ex, ey, tid);
+      s_nq[tid] = nb < 0 ? NN : max(NN, order_of<NN>(M, E.gb + nb));
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 4 * NMAX; idx += NT) {
+      const int f = idx / NMAX, q = idx % NMAX;
+      const int nq = s_nq[f];
+      if (q >= nq) continue;
+      const float* rule = X.rules + (size_t)nq * 3 * NMAX;
+      const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : rule[q];
+      const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : rule[q];
       const float hn = f < 2 ? X.hx : X.hy;          // velocity in reference units times this = u.n
       const float sg = (f == 0 || f == 2) ? -1.0f : 1.0f;
-      const float Wq = (f < 2 ? X.hy : X.hx) * s_w[q];
+      const float Wq = (f < 2 ? X.hy : X.hx) * rule[2 * NMAX + q];
       float uo = 0.0f, ui = 0.0f, p1 = 0.0f, p2 = 0.0f;
       const int S = c_rk_s[P.rk];
       for (int s = 0; s < S; ++s) {
@@ -311,6 +355,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
             for (int l = 0; l < NN; ++l) row = fmaf(s_psi[mm * NN + l], bx[l], row);
             val = fmaf(by[mm], row, val);
           }
+          val += fmaf(gx, (xr - 0.5f) + fdx, gy * ((yr - 0.5f) + fdy));   // phi - r0 = (L - r0) + psi
           p1 = fmaf(bw, val, p1);
           p2 = fmaf(bw * val, val, p2);
         } else if (un < -(float)TIE) {
@@ -323,16 +368,16 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P, const __grid
     if (tid < 16) {
       const int f = tid >> 2, k = tid & 3;
       float acc = 0.0f;
-      for (int q = 0; q < NN; ++q) acc += s_face[f][q][k];
-      W.faces[(size_t)e * 16 + tid] = acc;
+      for (int q = 0; q < s_nq[f]; ++q) acc += s_face[f][q][k];
+      W.faces[E.g * 16 + tid] = acc;
     }
   }
 }
 
 template <int NN>
-__global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid_constant__ Mixed2DExtra X,
-                                                     const float* __restrict__ in, Work2M W, float* __restrict__ out,
-                                                     unsigned* status) {
+__global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, const __grid_constant__ Mixed2DExtra X0,
+                                                     Map2D M, const float* __restrict__ in, Work2M W,
+                                                     float* __restrict__ out, unsigned* status) {
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
   constexpr int MMAX = 4 * NN + 1;
   __shared__ float s_xi[NN], s_w[NN], s_l0[NN], s_l1[NN];
@@ -341,17 +386,20 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
   __shared__ float s_red[NT / 32];
   __shared__ float s_scal[4];
   const int tid = threadIdx.x;
-  const int e = blockIdx.x;
-  const int ex = e % P.kx, ey = e / P.kx;
+  StepParams P = P0;
+  const Elem E = elem_of<NN>(P, M);
+  Mixed2DExtra X = X0;
+  batch_extra(P, M, X);
+  const int ex = E.ex, ey = E.ey;
   const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
   const float tn1T = X.tT + X.dtT;
   if (tid < NN) { s_xi[tid] = X.xi[tid]; s_w[tid] = X.w[tid]; s_l0[tid] = X.l0[tid]; s_l1[tid] = X.l1[tid]; }
   const bool part = tid < ND;
   const int i = tid % NN, j = tid / NN;
-  const float ref = W.elem[(size_t)e * 4];
+  const float ref = W.elem[E.g * 8], gx = W.elem[E.g * 8 + 1], gy = W.elem[E.g * 8 + 2];
   float ph = 0.0f;
   if (part) {
-    ph = W.psihat[(size_t)e * ND + tid];
+    ph = W.psihat[E.base + tid];
     s_ph[tid] = ph;
   }
   __syncthreads();
@@ -361,10 +409,22 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
   if (bnd && tid < 4 * NN) {
     const int f = tid / NN, q = tid % NN;
     const int nb = nb_index(P, ex, ey, f);
-    const float own = W.traces[(size_t)e * 4 * NN + tid];
-    // neighbour's trace relative to this element's reference value
-    const float other = nb >= 0 ? (W.elem[(size_t)nb * 4] - ref) + W.traces[(size_t)nb * 4 * NN + (f ^ 1) * NN + q]
-                                : (float)(P.ghost - (double)ref);
+    const float own = W.traces[E.g * M.tstride + tid];
+    // neighbour's value at this element's face points, relative to this element's reference L:
+    // (L_nb - L) in double (it is of the size of psi when both references fit the same data), plus
+    // the neighbour's trace of its own psihat
+    const double xq = X.xid[q];
+    const double fx = f == 0 ? 0.0 : f == 1 ? 1.0 : xq, fy = f == 2 ? 0.0 : f == 3 ? 1.0 : xq;
+    const double lown = lref(ref, gx, gy, fx, fy);
+    float other = (float)(P.ghost - lown);
+    if (nb >= 0) {
+      const int64_t gn = E.gb + nb;
+      const int nn = order_of<NN>(M, gn);
+      const float* tr = W.traces + gn * M.tstride + (f ^ 1) * nn;
+      const float* en = W.elem + gn * 8;
+      const double lnb = lref(en[0], en[1], en[2], f == 0 ? 1.0 : f == 1 ? 0.0 : fx, f == 2 ? 1.0 : f == 3 ? 0.0 : fy);
+      other = (float)(lnb - lown) + (nn == NN ? tr[q] : interp_rule(X.rules, nn, tr, s_xi[q]));
+    }
     const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : s_xi[q];
     const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : s_xi[q];
     float ur, vr;
@@ -381,14 +441,14 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
   if ((mass || energy) && tid == 0) {
     // net outflow of mass (increments) and of the squared increments, plus the velocity balance
     for (int f = 0; f < 4; ++f) {
-      const float* F = W.faces + (size_t)e * 16 + 4 * f;
+      const float* F = W.faces + E.g * 16 + 4 * f;
       const int nb = nb_index(P, ex, ey, f);
       nu += F[0] + F[1];
       netm += F[2];
       netd2 += F[3];
       if (nb >= 0) {
-        const float* G = W.faces + (size_t)nb * 16 + 4 * (f ^ 1);
-        const float dref = W.elem[(size_t)nb * 4] - ref;
+        const float* G = W.faces + (E.gb + nb) * 16 + 4 * (f ^ 1);
+        const float dref = W.elem[(E.gb + nb) * 8] - ref;
         // inflow part: u.n (dref + psi_nb) with the neighbour's u.n = -ours
         netm += dref * F[1] - G[2];
         netd2 += dref * dref * F[1] - 2.0f * dref * G[2] - G[3];
@@ -412,7 +472,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
     // target (increments): sum w psi^n - lam (net increment outflow + ref * closed-surface u.n)
     // ref * (closed-surface integral of u.n) is dropped: every 2D velocity here is divergence free
     // and the face quadrature integrates it to rounding; in float it would be noise of eps |U|
-    if (tid == 0) s_r[nb_rows] = (W.elem[(size_t)e * 4 + 1] - lam * netm) - mh;
+    if (tid == 0) s_r[nb_rows] = (W.elem[E.g * 8 + 3] - lam * netm) - mh;
   }
   __syncthreads();
   const int m = P.m;
@@ -427,11 +487,13 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
   if (energy) {
     // energy mismatch from increments (mass enforced): sum w (psiL - psi)(psiL + psi) + lam net(delta^2);
     // without the mass row, add 2 ref times the mass residual (closed-surface u.n taken as zero)
-    const float psin = part ? (in[(size_t)e * ND + tid] - ref) + in[X.plane + (size_t)e * ND + tid] : 0.0f;
+    const float psin = part ? (float)(((double)in[E.base + tid] + (double)in[X.plane + E.base + tid]) -
+                                      lref(ref, gx, gy, X.xid[i], X.xid[j]))
+                            : 0.0f;
     const float dpsi = part ? phL - psin : 0.0f;
     const float ev = block_sum<NT>(w2 * dpsi * (phL + (phL - dpsi)), s_red);
     const float ml = block_sum<NT>(w2 * phL, s_red);
-    const float m1 = W.elem[(size_t)e * 4 + 1];
+    const float m1 = W.elem[E.g * 8 + 3];
     float gamma;
     if (mass) gamma = ev + lam * netd2;
     else gamma = fmaf(2.0f * ref, (ml - m1) + lam * netm, ev + lam * netd2);
@@ -494,22 +556,21 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P, const __grid
     }
   }
   if (part) {
-    const float s = ref + cur;                // TwoSum: hi + lo == ref + cur exactly
-    const float bb = s - ref;
-    const float err = (ref - (s - bb)) + (cur - bb);
-    out[(size_t)e * ND + tid] = s;
-    out[X.plane + (size_t)e * ND + tid] = err;
+    const double v = lref(ref, gx, gy, X.xid[i], X.xid[j]) + (double)cur;   // L + psi, split into hi + lo
+    const float s = (float)v;
+    out[E.base + tid] = s;
+    out[X.plane + E.base + tid] = (float)(v - (double)s);
     if (!isfinite(s)) atomicOr(status, SL_ST_NONFINITE);
   }
   if (!ok && tid == 0) atomicOr(status, SL_ST_PICARD_NOCONV);
 }
 
 template <int NN>
-void launch_n(const StepParams& p, const Mixed2DExtra& x, const float* in, float* out, Work2M w, unsigned* st,
-              cudaStream_t s) {
-  const int nel = p.kx * p.ky;
-  k_p1<NN><<<nel, Shape<NN>::NT, 0, s>>>(p, x, in, w, st);
-  k_p2<NN><<<nel, Shape<NN>::NT, 0, s>>>(p, x, in, w, out, st);
+void launch_n(int phase, const StepParams& p, const Mixed2DExtra& x, const Map2D& m, int64_t count, const float* in,
+              float* out, const Work2M& w, unsigned* st, cudaStream_t s) {
+  if (count <= 0) return;
+  if (phase == 1) k_p1<NN><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, x, m, in, w, st);
+  else k_p2<NN><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, x, m, in, w, out, st);
 }
 
 }  // namespace k2m

@@ -32,8 +32,7 @@ size_t state_bytes(const sl_ctx* c) {
   return c->precision == SL_FP64 ? (size_t)c->nvals * sizeof(double) : (size_t)2 * plane_stride(c->nvals) * sizeof(float);
 }
 
-void max_speed(const sl_ctx* c, const sl_velocity* v, double& um, double& vm) {
-  const sl_mesh& M = c->mesh;
+void max_speed(const sl_mesh& M, const sl_velocity* v, double& um, double& vm) {
   um = vm = 0.0;
   switch (v->kind) {
     case SL_VEL_CONST: um = std::fabs(v->p[0]); vm = std::fabs(v->p[1]); break;
@@ -60,11 +59,200 @@ bool valid_velocity(const sl_ctx* c, const sl_velocity* v) {
   return true;
 }
 
+// Host and float table buffers of a context under construction.
+struct TableBufs {
+  std::vector<double> host;
+  std::vector<float> ftab;
+  size_t put(const std::vector<double>& v, size_t pad) {
+    size_t off = host.size();
+    host.insert(host.end(), v.begin(), v.end());
+    host.resize(off + std::max(pad, v.size()), 0.0);
+    host.resize((host.size() + 1) & ~size_t(1), 0.0);     // keep 16-byte alignment
+    return off;
+  }
+  size_t fput(const std::vector<double>& v) {
+    size_t off = ftab.size();
+    for (double x : v) ftab.push_back((float)x);
+    ftab.resize(off + std::max<size_t>(v.size(), NMAX), 0.0f);
+    ftab.resize((ftab.size() + 3) & ~size_t(3), 0.0f);
+    return off;
+  }
+};
+
+// basis and fit operators of node count n, appended to the table buffers (throws on failure)
+void build_ntab(sl_ntab& t, int n, int basis, int dim, bool mixed2d, TableBufs& B) {
+  t.present = true;
+  t.b = make_basis(n, basis);
+  for (unsigned mask = 0; mask < 4; ++mask)
+    for (int soft = 0; soft < 2; ++soft) {
+      if (dim == 1) {
+        t.fit[mask][soft] = make_fit_1d(t.b, mask);
+        finish_fit(t.fit[mask][soft], soft != 0);
+      } else {
+        t.fit[mask][soft] = make_fit_2d(t.b, mask, soft != 0);
+      }
+    }
+  t.off_xi = B.put(t.b.xi, NMAX);
+  t.off_w = B.put(t.b.w, NMAX);
+  t.off_lam = B.put(t.b.lam, NMAX);
+  t.off_l0 = B.put(t.b.l0, NMAX);
+  t.off_l1 = B.put(t.b.l1, NMAX);
+  for (int mask = 0; mask < 4; ++mask)
+    for (int soft = 0; soft < 2; ++soft) {
+      const FitOps& f = t.fit[mask][soft];
+      t.table_off[mask][soft][0] = B.put(f.Cpinv, 1);
+      t.table_off[mask][soft][1] = B.put(f.S, 1);
+      t.table_off[mask][soft][2] = B.put(f.SCt, 1);
+    }
+  if (mixed2d) {
+    t.f_off[0] = B.fput(t.b.xi);
+    t.f_off[1] = B.fput(t.b.lam);
+    t.f_off[2] = B.fput(t.b.w);
+    t.f_off[3] = B.fput(t.b.l0);
+    t.f_off[4] = B.fput(t.b.l1);
+    for (int mask = 0; mask < 4; ++mask) t.f_cp[mask] = B.fput(t.fit[mask][0].Cpinv);
+  }
+}
+
+// nodes, barycentric weights and quadrature weights of every node count, [NMAX + 1][3][NMAX]
+void build_rules(int basis, TableBufs& B, size_t& off, size_t& foff) {
+  std::vector<double> r((size_t)(NMAX + 1) * 3 * NMAX, 0.0);
+  for (int n = 2; n <= NMAX; ++n) {
+    const Basis1D b = make_basis(n, basis);
+    for (int i = 0; i < n; ++i) {
+      r[((size_t)n * 3 + 0) * NMAX + i] = b.xi[i];
+      r[((size_t)n * 3 + 1) * NMAX + i] = b.lam[i];
+      r[((size_t)n * 3 + 2) * NMAX + i] = b.w[i];
+    }
+  }
+  off = B.put(r, 1);
+  foff = B.fput(r);
+}
+
 }  // namespace
 
 namespace sl {
 void set_global_error(const std::string& msg) { g_init_err = msg; }
 }  // namespace sl
+
+namespace {
+
+// copy the tables of the context's own node count into the fields the uniform paths use
+void alias_ntab(sl_ctx* c) {
+  const sl_ntab& T = c->nt[c->n];
+  c->b = T.b;
+  for (int m = 0; m < 4; ++m)
+    for (int s = 0; s < 2; ++s) {
+      c->fit[m][s] = T.fit[m][s];
+      for (int k = 0; k < 3; ++k) c->table_off[m][s][k] = T.table_off[m][s][k];
+    }
+  c->off_xi = T.off_xi;
+  c->off_w = T.off_w;
+  c->off_lam = T.off_lam;
+  c->off_l0 = T.off_l0;
+  c->off_l1 = T.off_l1;
+  for (int k = 0; k < 5; ++k) c->f_off[k] = T.f_off[k];
+  for (int k = 0; k < 4; ++k) c->f_cp[k] = T.f_cp[k];
+}
+
+// device allocations and table upload; frees the context on failure
+sl_status alloc_upload(sl_ctx* c, const TableBufs& B, size_t work_bytes) {
+  c->red_blocks = 2 * 152;
+  if (cudaMalloc(&c->d_tables, B.host.size() * sizeof(double)) != cudaSuccess ||
+      (work_bytes && cudaMalloc(&c->d_work, work_bytes) != cudaSuccess) ||
+      (!B.ftab.empty() && cudaMalloc(&c->d_ftab, B.ftab.size() * sizeof(float)) != cudaSuccess) ||
+      cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&c->d_partial, c->red_blocks * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_result, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    sl_free(c);
+    return fail(nullptr, SL_ENOMEM, "device allocation failed");
+  }
+  if (cudaMemcpy(c->d_tables, B.host.data(), B.host.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!B.ftab.empty() &&
+       cudaMemcpy(c->d_ftab, B.ftab.data(), B.ftab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+    std::string msg = cudaGetErrorString(cudaGetLastError());
+    sl_free(c);
+    return fail(nullptr, SL_ECUDA, "table upload failed: " + msg);
+  }
+  return SL_OK;
+}
+
+sl_status finish_uniform(sl_ctx* c) {
+  const sl_mesh& M = c->mesh;
+  TableBufs B;
+  try {
+    build_ntab(c->nt[c->n], c->n, c->basis, M.dim, M.dim == 2 && c->precision == SL_MIXED, B);
+    if (M.dim == 2) build_rules(c->basis, B, c->off_rules, c->f_rules);
+  } catch (const std::exception& ex) {
+    std::string msg = ex.what();
+    delete c;
+    return fail(nullptr, SL_EINVAL, "table construction failed: " + msg);
+  }
+  alias_ntab(c);
+  const size_t work_bytes = M.dim != 2 ? 0
+                            : c->precision == SL_FP64 ? work2d_doubles(c->nel, c->n) * sizeof(double)
+                                                      : work2m_floats(c->nel, c->n) * sizeof(float);
+  return alloc_upload(c, B, work_bytes);
+}
+
+// p-adaptive meshes and batches: tables of every node count present, node-count buckets, the
+// element map on the device.  prob: problem of each element (batches; empty for one problem).
+sl_status finish_mapped(sl_ctx* c, const std::vector<uint16_t>& prob = {}) {
+  c->mapped = true;
+  const int64_t nel = c->nel;
+  bool present[NMAX + 1] = {};
+  for (uint8_t o : c->ord_host) present[o] = true;
+  TableBufs B;
+  try {
+    for (int n = 2; n <= NMAX; ++n)
+      if (present[n]) build_ntab(c->nt[n], n, c->basis, 2, c->precision == SL_MIXED, B);
+    build_rules(c->basis, B, c->off_rules, c->f_rules);
+  } catch (const std::exception& ex) {
+    std::string msg = ex.what();
+    delete c;
+    return fail(nullptr, SL_EINVAL, "table construction failed: " + msg);
+  }
+  alias_ntab(c);
+  // elements by node count (ascending), each bucket in element order
+  std::vector<int> list(nel);
+  int64_t pos = 0;
+  for (int n = 2; n <= NMAX; ++n) {
+    c->bucket_start[n] = pos;
+    for (int64_t g = 0; g < nel; ++g)
+      if (c->ord_host[g] == n) list[pos++] = (int)g;
+    c->bucket_count[n] = pos - c->bucket_start[n];
+  }
+  const size_t work_bytes = c->precision == SL_FP64
+                                ? (size_t)(c->nvals + nel * (4 * NMAX + 8)) * sizeof(double)
+                                : (size_t)(c->nvals + nel * (4 * NMAX + 16 + 8)) * sizeof(float);
+  sl_status st = alloc_upload(c, B, work_bytes);
+  if (st != SL_OK) return st;
+  const bool batch = !prob.empty();
+  if (cudaMalloc(&c->d_off, (nel + 1) * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&c->d_ord, nel * sizeof(uint8_t)) != cudaSuccess ||
+      cudaMalloc(&c->d_list, nel * sizeof(int)) != cudaSuccess ||
+      (batch && cudaMalloc(&c->d_prob, nel * sizeof(uint16_t)) != cudaSuccess) ||
+      (batch && cudaMalloc(&c->d_geo, c->geo_host.size() * sizeof(ProbGeom)) != cudaSuccess)) {
+    cudaGetLastError();
+    sl_free(c);
+    return fail(nullptr, SL_ENOMEM, "device allocation of the element map failed");
+  }
+  if (cudaMemcpy(c->d_off, c->off_host.data(), (nel + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_ord, c->ord_host.data(), nel * sizeof(uint8_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_list, list.data(), nel * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (batch && cudaMemcpy(c->d_prob, prob.data(), nel * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (batch && cudaMemcpy(c->d_geo, c->geo_host.data(), c->geo_host.size() * sizeof(ProbGeom),
+                           cudaMemcpyHostToDevice) != cudaSuccess)) {
+    std::string msg = cudaGetErrorString(cudaGetLastError());
+    sl_free(c);
+    return fail(nullptr, SL_ECUDA, "element map upload failed: " + msg);
+  }
+  return SL_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -84,96 +272,47 @@ sl_status sl_init(const sl_mesh* mesh, int n, int basis, int precision, void* cu
     return fail(nullptr, SL_EINVAL, "periodic faces must come in pairs");
   if (basis != SL_GAUSS_LEGENDRE && basis != SL_CHEB_GAUSS) return fail(nullptr, SL_EINVAL, "bad basis");
   if (precision != SL_FP64 && precision != SL_MIXED) return fail(nullptr, SL_EINVAL, "bad precision");
-  if (mesh->order) return fail(nullptr, SL_EUNSUPPORTED, "p-adaptive meshes are not built yet");
-  if (n < 2 || n > NMAX) return fail(nullptr, SL_EINVAL, "n must lie in [2, 17]");
+  if (mesh->order && mesh->dim != 2) return fail(nullptr, SL_EUNSUPPORTED, "p-adaptive meshes are two-dimensional");
+  if (!mesh->order && (n < 2 || n > NMAX)) return fail(nullptr, SL_EINVAL, "n must lie in [2, 17]");
   if ((int64_t)mesh->kx * mesh->ky > (int64_t)1 << 31) return fail(nullptr, SL_EINVAL, "too many elements");
+  if (mesh->order)
+    for (int64_t g = 0; g < (int64_t)mesh->kx * mesh->ky; ++g)
+      if (mesh->order[g] < 2 || mesh->order[g] > NMAX)
+        return fail(nullptr, SL_EINVAL, "per-element node counts must lie in [2, 17]");
 
   sl_ctx* c = new (std::nothrow) sl_ctx();
   if (!c) return fail(nullptr, SL_ENOMEM, "host allocation failed");
   c->mesh = *mesh;
   c->mesh.order = nullptr;
-  c->n = n;
   c->basis = basis;
   c->precision = precision;
   c->stream = (cudaStream_t)cuda_stream;
   const int64_t nel = (int64_t)mesh->kx * mesh->ky;
-  const int nd = mesh->dim == 1 ? n : n * n;
-  c->nvals = nel * nd;
-  try {
-    c->b = make_basis(n, basis);
-    for (unsigned mask = 0; mask < 4; ++mask)
-      for (int soft = 0; soft < 2; ++soft) {
-        if (mesh->dim == 1) {
-          c->fit[mask][soft] = make_fit_1d(c->b, mask);
-          finish_fit(c->fit[mask][soft], soft != 0);
-        } else {
-          c->fit[mask][soft] = make_fit_2d(c->b, mask, soft != 0);
-        }
-      }
-  } catch (const std::exception& ex) {
-    std::string msg = ex.what();
-    delete c;
-    return fail(nullptr, SL_EINVAL, "table construction failed: " + msg);
-  }
-  // one device buffer: basis tables then per (mask, mode) operators
-  std::vector<double> host;
-  auto put = [&](const std::vector<double>& v, size_t pad) {
-    size_t off = host.size();
-    host.insert(host.end(), v.begin(), v.end());
-    host.resize(off + std::max(pad, v.size()), 0.0);
-    host.resize((host.size() + 1) & ~size_t(1), 0.0);     // keep 16-byte alignment
-    return off;
-  };
-  c->off_xi = put(c->b.xi, NMAX);
-  c->off_w = put(c->b.w, NMAX);
-  c->off_lam = put(c->b.lam, NMAX);
-  c->off_l0 = put(c->b.l0, NMAX);
-  c->off_l1 = put(c->b.l1, NMAX);
-  for (int mask = 0; mask < 4; ++mask)
-    for (int soft = 0; soft < 2; ++soft) {
-      const FitOps& f = c->fit[mask][soft];
-      c->table_off[mask][soft][0] = put(f.Cpinv, 1);
-      c->table_off[mask][soft][1] = put(f.S, 1);
-      c->table_off[mask][soft][2] = put(f.SCt, 1);
+  c->nel = nel;
+  if (mesh->order) {
+    c->orders.assign(mesh->order, mesh->order + nel);
+    c->ord_host.resize(nel);
+    c->off_host.resize(nel + 1);
+    int64_t acc = 0;
+    int nmax = 2;
+    for (int64_t g = 0; g < nel; ++g) {
+      const int o = mesh->order[g];
+      c->ord_host[g] = (uint8_t)o;
+      c->off_host[g] = acc;
+      acc += (int64_t)o * o;
+      nmax = std::max(nmax, o);
     }
-  c->red_blocks = 2 * 152;
-  // float copies of the tables for the mixed 2D kernels
-  std::vector<float> ftab;
-  auto fput = [&](const std::vector<double>& v) {
-    size_t off = ftab.size();
-    for (double x : v) ftab.push_back((float)x);
-    ftab.resize(off + std::max<size_t>(v.size(), NMAX), 0.0f);
-    ftab.resize((ftab.size() + 3) & ~size_t(3), 0.0f);
-    return off;
-  };
-  if (mesh->dim == 2 && precision == SL_MIXED) {
-    c->f_off[0] = fput(c->b.xi);
-    c->f_off[1] = fput(c->b.lam);
-    c->f_off[2] = fput(c->b.w);
-    c->f_off[3] = fput(c->b.l0);
-    c->f_off[4] = fput(c->b.l1);
-    for (int mask = 0; mask < 4; ++mask) c->f_cp[mask] = fput(c->fit[mask][0].Cpinv);
-  }
-  const size_t work_bytes = mesh->dim != 2 ? 0
-                            : precision == SL_FP64 ? work2d_doubles(nel, n) * sizeof(double)
-                                                   : work2m_floats(nel, n) * sizeof(float);
-  if (cudaMalloc(&c->d_tables, host.size() * sizeof(double)) != cudaSuccess ||
-      (work_bytes && cudaMalloc(&c->d_work, work_bytes) != cudaSuccess) ||
-      (!ftab.empty() && cudaMalloc(&c->d_ftab, ftab.size() * sizeof(float)) != cudaSuccess) ||
-      cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&c->d_partial, c->red_blocks * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->d_result, sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    sl_free(c);
-    return fail(nullptr, SL_ENOMEM, "device allocation failed");
-  }
-  if (cudaMemcpy(c->d_tables, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-      (!ftab.empty() &&
-       cudaMemcpy(c->d_ftab, ftab.data(), ftab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) ||
-      cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
-    std::string msg = cudaGetErrorString(cudaGetLastError());
-    sl_free(c);
-    return fail(nullptr, SL_ECUDA, "table upload failed: " + msg);
+    c->off_host[nel] = acc;
+    c->n = nmax;
+    c->nvals = acc;
+    c->prob_mesh.assign(1, c->mesh);
+    sl_status st = finish_mapped(c);
+    if (st != SL_OK) return st;
+  } else {
+    c->n = n;
+    c->nvals = nel * (mesh->dim == 1 ? n : n * n);
+    sl_status st = finish_uniform(c);
+    if (st != SL_OK) return st;
   }
   *out = c;
   return SL_OK;
@@ -190,28 +329,178 @@ void sl_free(sl_ctx* c) {
   cudaFree(c->d_work);
   cudaFree(c->d_ftab);
   cudaFree(c->d_m2c);
+  cudaFree(c->d_off);
+  cudaFree(c->d_ord);
+  cudaFree(c->d_prob);
+  cudaFree(c->d_geo);
+  cudaFree(c->d_list);
   delete c;
 }
 
-sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocity* vel, double t, double dt,
-                  const sl_options* opt) {
-  if (!c) return SL_EINVAL;
+sl_status sl_batch_create(int nprob, sl_ctx* const* probs, sl_ctx** out) {
+  if (!out) return fail(nullptr, SL_EINVAL, "out is null");
+  *out = nullptr;
+  if (nprob < 1 || nprob > 65535 || !probs) return fail(nullptr, SL_EINVAL, "need 1..65535 problems");
+  for (int p = 0; p < nprob; ++p) {
+    const sl_ctx* q = probs[p];
+    if (!q) return fail(nullptr, SL_EINVAL, "null problem context");
+    if (q->mesh.dim != 2) return fail(nullptr, SL_EUNSUPPORTED, "batches are of 2D problems");
+    if (!q->geo_host.empty()) return fail(nullptr, SL_EINVAL, "a batch cannot contain a batch");
+    if (q->basis != probs[0]->basis || q->precision != probs[0]->precision)
+      return fail(nullptr, SL_EINVAL, "the problems of a batch share basis and precision");
+  }
+  sl_ctx* c = new (std::nothrow) sl_ctx();
+  if (!c) return fail(nullptr, SL_ENOMEM, "host allocation failed");
+  c->mesh = probs[0]->mesh;
+  c->basis = probs[0]->basis;
+  c->precision = probs[0]->precision;
+  c->stream = probs[0]->stream;
+  c->nprob = nprob;
+  std::vector<uint16_t> prob;
+  int64_t gb = 0, acc = 0;
+  int nmax = 2;
+  try {
+    for (int p = 0; p < nprob; ++p) {
+      const sl_ctx* q = probs[p];
+      const sl_mesh& M = q->mesh;
+      ProbGeom G{};
+      G.kx = M.kx;
+      G.ky = M.ky;
+      for (int f = 0; f < 4; ++f) G.bc[f] = M.bc[f];
+      G.x0 = M.x0;
+      G.hx = (M.x1 - M.x0) / M.kx;
+      G.y0 = M.y0;
+      G.hy = (M.y1 - M.y0) / M.ky;
+      G.ghost = M.ghost;
+      G.gbase = gb;
+      c->geo_host.push_back(G);
+      c->prob_mesh.push_back(M);
+      for (int64_t g = 0; g < q->nel; ++g) {
+        const int o = q->mapped ? q->ord_host[g] : q->n;
+        c->ord_host.push_back((uint8_t)o);
+        c->off_host.push_back(acc);
+        prob.push_back((uint16_t)p);
+        acc += (int64_t)o * o;
+        nmax = std::max(nmax, o);
+      }
+      gb += q->nel;
+    }
+  } catch (const std::exception&) {
+    delete c;
+    return fail(nullptr, SL_ENOMEM, "host allocation failed");
+  }
+  if (gb > (int64_t)1 << 31) {
+    delete c;
+    return fail(nullptr, SL_EINVAL, "too many elements");
+  }
+  c->off_host.push_back(acc);
+  c->nel = gb;
+  c->nvals = acc;
+  c->n = nmax;
+  sl_status st = finish_mapped(c, prob);
+  if (st != SL_OK) return st;
+  *out = c;
+  return SL_OK;
+}
+
+int64_t sl_batch_offset(const sl_ctx* c, int p) {
+  if (!c || p < 0 || p > c->nprob || c->geo_host.empty()) return -1;
+  if (p == c->nprob) return c->nvals;
+  return c->off_host[c->geo_host[p].gbase];
+}
+
+}  // extern "C"
+
+namespace {
+
+sl_status check_step(sl_ctx* c, const void* phi_in, const void* phi_out, const sl_velocity* vel,
+                     const sl_options* opt) {
   if (!phi_in || !phi_out || !opt) return fail(c, SL_EINVAL, "null argument");
   if (phi_in == phi_out) return fail(c, SL_EINVAL, "phi_in and phi_out must be distinct buffers");
   if (!valid_velocity(c, vel)) return fail(c, SL_EINVAL, "bad velocity for this mesh");
-  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t)) return fail(c, SL_EINVAL, "dt must be finite and > 0");
   if (opt->rk_order < 1 || opt->rk_order > 4) return fail(c, SL_EINVAL, "rk_order must be 1..4");
   if (opt->fit != SL_FIT_HARD && opt->fit != SL_FIT_SOFT) return fail(c, SL_EINVAL, "bad fit mode");
   if (opt->bvalue != SL_BV_INTERP && opt->bvalue != SL_BV_BACKTRACK) return fail(c, SL_EINVAL, "bad bvalue");
   if (opt->constraints & ~7u) return fail(c, SL_EINVAL, "unknown constraint bits");
   if (opt->picard_rtol < 0.0 || opt->picard_cap < 0) return fail(c, SL_EINVAL, "bad energy iteration limits");
-  const sl_mesh& M = c->mesh;
+  return SL_OK;
+}
+
+// time and step of one problem: finite, positive, displacement within one element width
+sl_status check_dt(sl_ctx* c, const sl_mesh& M, const sl_velocity* vel, double t, double dt) {
+  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t)) return fail(c, SL_EINVAL, "dt must be finite and > 0");
   const double hx = (M.x1 - M.x0) / M.kx, hy = M.dim == 2 ? (M.y1 - M.y0) / M.ky : 1.0;
   double um, vm;
-  max_speed(c, vel, um, vm);
+  max_speed(M, vel, um, vm);
   if (um * dt > hx || (M.dim == 2 && vm * dt > hy))
     return fail(c, SL_ECFL, "displacement over the step exceeds one element width");
+  return SL_OK;
+}
 
+// the general 2D kernels: phase 1 of every node-count bucket, then phase 2 of every bucket
+void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, double dt, const sl_options* opt,
+                    const void* in, void* out) {
+  const unsigned lin = opt->constraints & 3u;
+  const int soft = opt->fit == SL_FIT_SOFT ? 1 : 0;
+  const int64_t nel = c->nel;
+  Map2D map{};
+  int ts = 4 * c->n;
+  if (c->mapped) {
+    map.off = c->d_off;
+    map.ord = c->d_ord;
+    map.prob = c->d_prob;
+    map.geo = c->d_geo;
+    ts = 4 * NMAX;
+  }
+  map.tstride = ts;
+  const double* T = c->d_tables;
+  const float* F = c->d_ftab;
+  const sl_mesh& M = c->mesh;
+  const double hx = (M.x1 - M.x0) / M.kx, hy = (M.y1 - M.y0) / M.ky;
+  for (int phase = 1; phase <= 2; ++phase)
+    for (int n = 2; n <= NMAX; ++n) {
+      int64_t count;
+      if (c->mapped) {
+        count = c->bucket_count[n];
+        if (count == 0) continue;
+        map.list = c->d_list + c->bucket_start[n];
+      } else {
+        if (n != c->n) continue;
+        count = nel;
+        map.list = nullptr;
+      }
+      const sl_ntab& N = c->nt[n];
+      P.m = N.fit[lin][soft].m;
+      if (c->precision == SL_FP64) {
+        const size_t* off = N.table_off[lin][soft];
+        Tables1D tb{T + N.off_xi, T + N.off_w, T + N.off_lam, T + N.off_l0, T + N.off_l1,
+                    T + off[0],   T + off[1],  T + off[2],    T + c->off_rules};
+        double* W = c->d_work;
+        Work2D w{W, W + c->nvals, W + c->nvals + nel * ts};
+        launch_step2d_f64(phase, n, P, tb, map, count, (const double*)in, (double*)out, w, c->d_status, c->stream);
+      } else {
+        Mixed2DExtra X{F + N.f_off[0], F + N.f_off[1], F + N.f_off[2], F + N.f_off[3], F + N.f_off[4],
+                       F + N.f_cp[lin], F + c->f_rules, T + N.off_xi,
+                       (opt->constraints & SL_C_ENERGY) ? 0 : 1, plane_stride(c->nvals),
+                       (float)hx, (float)hy, (float)(1.0 / hx), (float)(1.0 / hy),
+                       (float)vel->p[0], (float)vel->p[1], (float)vel->p[0], (float)vel->p[1], (float)vel->p[2],
+                       0.0f, 0.0f, (float)dt, (float)(dt / (hx * hy)), 0.0};
+        if (vel->kind == SL_VEL_SWIRL) {
+          X.tT = (float)(t / vel->p[0]);
+          X.dtT = (float)(dt / vel->p[0]);
+          X.Tper = vel->p[0];
+        }
+        float* W = (float*)c->d_work;
+        Work2M w{W, W + c->nvals, W + c->nvals + nel * ts, W + c->nvals + nel * (ts + 16)};
+        launch_step2d_mixed(phase, n, P, X, map, count, (const float*)in, (float*)out, w, c->d_status, c->stream);
+      }
+    }
+}
+
+sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocity* vel, double t, double dt,
+                        const sl_options* opt) {
+  const sl_mesh& M = c->mesh;
+  const double hx = (M.x1 - M.x0) / M.kx, hy = M.dim == 2 ? (M.y1 - M.y0) / M.ky : 1.0;
   StepParams P{};
   P.K = M.kx;
   P.kx = M.kx;
@@ -266,10 +555,8 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
   } else if (M.dim == 2 && c->precision == SL_FP64) {
     if (opt->bvalue != SL_BV_INTERP)
       return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
-    Tables1D tb{T + c->off_xi, T + c->off_w, T + c->off_lam, T + c->off_l0, T + c->off_l1,
-                T + off[0], T + off[1], T + off[2]};
-    launch_step2d_f64(c->n, P, tb, (const double*)phi_in, (double*)phi_out, c->d_work, c->d_status, c->stream);
-  } else if (M.dim == 2 && c->precision == SL_MIXED && vel->kind == SL_VEL_CONST && vel->p[0] != 0.0 &&
+    step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
+  } else if (M.dim == 2 && c->precision == SL_MIXED && !c->mapped && vel->kind == SL_VEL_CONST && vel->p[0] != 0.0 &&
              vel->p[1] != 0.0 && opt->fit == SL_FIT_HARD && !(opt->constraints & SL_C_ENERGY) &&
              opt->bvalue == SL_BV_INTERP && (opt->constraints & 3u)) {
     // uniform mesh, constant velocity: one operator shared by all elements
@@ -303,23 +590,56 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
     if (opt->bvalue != SL_BV_INTERP)
       return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
     if (opt->fit != SL_FIT_HARD) return fail(c, SL_EUNSUPPORTED, "the 2D mixed path uses the hard fit");
-    const float* F = c->d_ftab;
-    Mixed2DExtra X{F + c->f_off[0], F + c->f_off[1], F + c->f_off[2], F + c->f_off[3], F + c->f_off[4],
-                   F + c->f_cp[lin], plane_stride(c->nvals),
-                   (float)hx, (float)hy, (float)(1.0 / hx), (float)(1.0 / hy),
-                   (float)vel->p[0], (float)vel->p[1], (float)vel->p[0], (float)vel->p[1], (float)vel->p[2],
-                   0.0f, 0.0f, (float)dt, (float)(dt / (hx * hy))};
-    if (vel->kind == SL_VEL_SWIRL) {
-      X.tT = (float)(t / vel->p[0]);
-      X.dtT = (float)(dt / vel->p[0]);
-    }
-    launch_step2d_mixed(c->n, P, X, (const float*)phi_in, (float*)phi_out, (float*)c->d_work, c->d_status,
-                        c->stream);
+    step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
   } else {
     return fail(c, SL_EUNSUPPORTED, "this dimension/precision combination is not built yet");
   }
   SL_CUDA(c, cudaGetLastError());
   return SL_OK;
+}
+
+// per-problem times and steps of a batch into its device geometry table
+sl_status set_batch_steps(sl_ctx* c, const sl_velocity* vel, const double* t, const double* dt) {
+  for (int p = 0; p < c->nprob; ++p) {
+    sl_status st = check_dt(c, c->prob_mesh[p], vel, t[p], dt[p]);
+    if (st != SL_OK) return st;
+    c->geo_host[p].t = t[p];
+    c->geo_host[p].dt = dt[p];
+  }
+  SL_CUDA(c, cudaMemcpyAsync(c->d_geo, c->geo_host.data(), c->geo_host.size() * sizeof(ProbGeom),
+                             cudaMemcpyHostToDevice, c->stream));
+  return SL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocity* vel, double t, double dt,
+                  const sl_options* opt) {
+  if (!c) return SL_EINVAL;
+  sl_status st = check_step(c, phi_in, phi_out, vel, opt);
+  if (st != SL_OK) return st;
+  if (!c->geo_host.empty()) {
+    std::vector<double> ts(c->nprob, t), dts(c->nprob, dt);
+    st = set_batch_steps(c, vel, ts.data(), dts.data());
+  } else {
+    st = check_dt(c, c->mesh, vel, t, dt);
+  }
+  if (st != SL_OK) return st;
+  return step_dispatch(c, phi_in, phi_out, vel, t, dt, opt);
+}
+
+sl_status sl_batch_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocity* vel, const double* t,
+                        const double* dt, const sl_options* opt) {
+  if (!c) return SL_EINVAL;
+  if (c->geo_host.empty()) return fail(c, SL_EINVAL, "not a batch context");
+  if (!t || !dt) return fail(c, SL_EINVAL, "null argument");
+  sl_status st = check_step(c, phi_in, phi_out, vel, opt);
+  if (st != SL_OK) return st;
+  st = set_batch_steps(c, vel, t, dt);
+  if (st != SL_OK) return st;
+  return step_dispatch(c, phi_in, phi_out, vel, t[0], dt[0], opt);
 }
 
 sl_status sl_run_host(sl_ctx* c, const double* host_in, double* host_out, const sl_velocity* vel, double t0,
@@ -394,7 +714,11 @@ static sl_status integral(sl_ctx* c, const void* phi, double* total, int power) 
   const sl_mesh& M = c->mesh;
   const double hx = (M.x1 - M.x0) / M.kx, hy = M.dim == 2 ? (M.y1 - M.y0) / M.ky : 1.0;
   const int64_t nel = (int64_t)M.kx * M.ky;
-  if (c->precision == SL_FP64)
+  if (c->mapped)
+    launch_mass_energy_csr(c->nel, c->d_off, c->d_ord, c->d_prob, c->d_geo, hx * hy, c->precision,
+                           plane_stride(c->nvals), phi, c->d_tables + c->off_rules, power, c->d_partial, c->d_result,
+                           c->red_blocks, c->stream);
+  else if (c->precision == SL_FP64)
     launch_mass_energy_f64(nel, c->n, (const double*)phi, c->d_tables + c->off_w, M.dim, power, hx * hy,
                            c->d_partial, c->d_result, c->red_blocks, c->stream);
   else
@@ -423,20 +747,24 @@ sl_status sl_max_dt(const sl_ctx* c, const sl_velocity* vel, int rule, double* d
   if (!c || !dt) return SL_EINVAL;
   if (!valid_velocity(c, vel)) return fail(const_cast<sl_ctx*>(c), SL_EINVAL, "bad velocity");
   if (rule != SL_RULE_HALF_MIN_SPACING && rule != SL_RULE_PAPER) return fail(const_cast<sl_ctx*>(c), SL_EINVAL, "bad rule");
-  const std::vector<double>& xi = c->b.xi;
-  double gap;
-  if (rule == SL_RULE_PAPER) gap = xi[0];
-  else {
-    gap = 1.0;
-    for (size_t i = 1; i < xi.size(); ++i) gap = std::min(gap, xi[i] - xi[i - 1]);
+  // smallest gap over the node counts in use: edge node to face (paper) or between nodes
+  double gap = 1.0;
+  for (int n = 2; n <= NMAX; ++n) {
+    if (!c->nt[n].present) continue;
+    const std::vector<double>& xi = c->nt[n].b.xi;
+    if (rule == SL_RULE_PAPER) gap = std::min(gap, xi[0]);
+    else
+      for (size_t i = 1; i < xi.size(); ++i) gap = std::min(gap, xi[i] - xi[i - 1]);
   }
   const double factor = rule == SL_RULE_PAPER ? 1.0 : 0.5;
-  const sl_mesh& M = c->mesh;
-  double um, vm;
-  max_speed(c, vel, um, vm);
   double lim = INFINITY;
-  if (um > 0) lim = std::min(lim, (M.x1 - M.x0) / M.kx * gap / um);
-  if (M.dim == 2 && vm > 0) lim = std::min(lim, (M.y1 - M.y0) / M.ky * gap / vm);
+  const std::vector<sl_mesh> one(1, c->mesh);
+  for (const sl_mesh& M : c->prob_mesh.empty() ? one : c->prob_mesh) {
+    double um, vm;
+    max_speed(M, vel, um, vm);
+    if (um > 0) lim = std::min(lim, (M.x1 - M.x0) / M.kx * gap / um);
+    if (M.dim == 2 && vm > 0) lim = std::min(lim, (M.y1 - M.y0) / M.ky * gap / vm);
+  }
   if (!std::isfinite(lim)) return fail(const_cast<sl_ctx*>(c), SL_EINVAL, "velocity is zero everywhere");
   *dt = factor * lim;
   return SL_OK;
@@ -450,20 +778,29 @@ sl_status sl_node_coords(const sl_ctx* c, double* x, double* y) {
   if (!c || !x || (c->mesh.dim == 2 && !y)) return SL_EINVAL;
   const sl_mesh& M = c->mesh;
   const int n = c->n;
-  const double hx = (M.x1 - M.x0) / M.kx, hy = M.dim == 2 ? (M.y1 - M.y0) / M.ky : 1.0;
   if (M.dim == 1) {
+    const double hx = (M.x1 - M.x0) / M.kx;
     for (int k = 0; k < M.kx; ++k)
       for (int i = 0; i < n; ++i) x[(int64_t)k * n + i] = M.x0 + (k + c->b.xi[i]) * hx;
     return SL_OK;
   }
-  for (int ey = 0; ey < M.ky; ++ey)
-    for (int ex = 0; ex < M.kx; ++ex)
-      for (int j = 0; j < n; ++j)
-        for (int i = 0; i < n; ++i) {
-          const int64_t o = (((int64_t)ey * M.kx + ex) * n + j) * n + i;
-          x[o] = M.x0 + (ex + c->b.xi[i]) * hx;
-          y[o] = M.y0 + (ey + c->b.xi[j]) * hy;
-        }
+  const std::vector<sl_mesh> one(1, c->mesh);
+  const std::vector<sl_mesh>& meshes = c->prob_mesh.empty() ? one : c->prob_mesh;
+  int64_t g = 0;
+  for (const sl_mesh& P : meshes) {
+    const double hx = (P.x1 - P.x0) / P.kx, hy = (P.y1 - P.y0) / P.ky;
+    for (int ey = 0; ey < P.ky; ++ey)
+      for (int ex = 0; ex < P.kx; ++ex, ++g) {
+        const int m = c->mapped ? c->ord_host[g] : n;
+        const std::vector<double>& xi = c->nt[m].b.xi;
+        const int64_t o0 = c->mapped ? c->off_host[g] : g * n * n;
+        for (int j = 0; j < m; ++j)
+          for (int i = 0; i < m; ++i) {
+            x[o0 + j * m + i] = P.x0 + (ex + xi[i]) * hx;
+            y[o0 + j * m + i] = P.y0 + (ey + xi[j]) * hy;
+          }
+      }
+  }
   return SL_OK;
 }
 

@@ -56,6 +56,7 @@ struct Tables1D {                         // device pointers into one table buff
   const double* Cpinv;                   // [n][m] for the active row set
   const double* S;                       // [n][n]
   const double* SCt;                     // [n][m]
+  const double* rules;                   // [NMAX + 1][3][NMAX] xi, lam, w of every node count
 };
 
 struct StepParams {
@@ -79,9 +80,39 @@ struct StepParams {
 void launch_step1d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in,
                        double* out, unsigned* status, cudaStream_t s);
 
-// 2D FP64 step (two kernels); work holds nel * (n^2 + 4n + 8) doubles
-void launch_step2d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in, double* out, double* work,
-                       unsigned* status, cudaStream_t s);
+// Geometry and step of one problem of a batch (device array); replaces the StepParams fields of
+// the same names for the elements of that problem.
+struct ProbGeom {
+  int kx, ky;
+  int bc[4];
+  double x0, hx, y0, hy;
+  double ghost, t, dt;
+  int64_t gbase;                         // global index of the problem's first element
+};
+
+// Element map of a 2D launch of the general kernels.  A uniform single-problem mesh uses the
+// null map (CTA b advances element b, values at b n^2); p-adaptive meshes (per-element node
+// counts, CSR value offsets) and batches of problems launch once per node count with the list
+// of elements of that count.
+struct Map2D {
+  const int* list;                       // global indices of the elements this launch advances
+  const int64_t* off;                    // value offset of each element (null: g n^2)
+  const uint8_t* ord;                    // node count of each element (null: all the launch's n)
+  const uint16_t* prob;                  // problem of each element (null: the StepParams problem)
+  const ProbGeom* geo;                   // per-problem geometry and step (null: StepParams)
+  int tstride;                           // trace values per element in the workspace
+};
+
+struct Work2D {                          // FP64 workspace between the two phases
+  double* phihat;                        // same layout as the state
+  double* traces;                        // [nel][tstride]   faces W, E, S, N at the tangential nodes
+  double* fluxes;                        // [nel][4][2]      outflow (mass, energy) flux per face
+};
+
+// 2D FP64 step: phase 1 (remap, traces, outflow fluxes) of every launch must run before any
+// phase 2 (interface values, targets, fit); count = CTAs (elements) of the launch
+void launch_step2d_f64(int phase, int n, const StepParams& p, const Tables1D& tb, const Map2D& m, int64_t count,
+                       const double* in, double* out, const Work2D& w, unsigned* status, cudaStream_t s);
 inline int64_t work2d_doubles(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 8); }
 
 // Extra parameters of the 2D mixed-precision kernels (float tables and scalars), by value
@@ -92,15 +123,26 @@ struct Mixed2DExtra {
   const float* l0;
   const float* l1;
   const float* Cp;                       // [n^2][m] pseudo-inverse of the active rows (hard fit)
+  const float* rules;                    // [NMAX + 1][3][NMAX] xi, lam, w of every node count
+  const double* xid;                     // the nodes again, in double (element reference values)
+  int linref;                            // 1: linear element reference (no energy row), 0: constant
   int64_t plane;                         // float offset of the lo plane
   float hx, hy, ihx, ihy;
   float a, b, om, cx, cy;                // velocity parameters (constant / rotation)
   float tT, dtT;                         // t / T and dt / T (swirl)
   float dt, dt_area;                     // dt and dt / (hx hy)
+  double Tper;                           // swirl period T (per-problem t / T in a batch), else 0
 };
-void launch_step2d_mixed(int n, const StepParams& p, const Mixed2DExtra& x, const float* in, float* out, float* work,
-                         unsigned* status, cudaStream_t s);
-inline int64_t work2m_floats(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 16 + 4); }
+struct Work2M {                          // mixed workspace between the two phases
+  float* psihat;                         // same layout as the state (one plane)
+  float* traces;                         // [nel][tstride]
+  float* faces;                          // [nel][4][4]  U_out, U_in, Psi, Psi2 per face
+  float* elem;                           // [nel][8]     r0, gx, gy, sum w psi, sum w psi^2, unused
+};
+void launch_step2d_mixed(int phase, int n, const StepParams& p, const Mixed2DExtra& x, const Map2D& m,
+                         int64_t count, const float* in, float* out, const Work2M& w, unsigned* status,
+                         cudaStream_t s);
+inline int64_t work2m_floats(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 16 + 8); }
 
 // Parameters of the 2D shared-operator kernel (uniform mesh, constant velocity).  Operators that
 // every thread applies with the same entry live here (the kernel reads them from the parameter
@@ -155,10 +197,26 @@ void launch_mass_energy_f64(int64_t nelem, int nper, const double* phi, const do
 void launch_mass_energy_pair(int64_t nelem, int nper, int64_t plane, const float* phi, const double* w,
                              int dim, int power, double scale, double* partial, double* result,
                              int nblocks, cudaStream_t s);
+void launch_mass_energy_csr(int64_t nel, const int64_t* off, const uint8_t* ord, const uint16_t* prob,
+                            const ProbGeom* geo, double area, int precision, int64_t plane, const void* phi,
+                            const double* rules, int power, double* partial, double* result, int nblocks,
+                            cudaStream_t s);
 
 }  // namespace sl
 
 // ------------------------------------------------------------------ context
+
+// Tables of one node count: basis, fit operators per constraint mask and mode, and their offsets
+// in the context's device table buffers.
+struct sl_ntab {
+  bool present = false;
+  sl::Basis1D b;
+  sl::FitOps fit[4][2];                  // [linear-row mask][soft]
+  size_t off_xi = 0, off_w = 0, off_lam = 0, off_l0 = 0, off_l1 = 0;   // doubles
+  size_t table_off[4][2][3] = {};        // Cpinv, S, SCt per mask / mode (doubles)
+  size_t f_off[5] = {};                  // xi, lam, w, l0, l1 (floats, mixed 2D)
+  size_t f_cp[4] = {};                   // float pseudo-inverse per linear-row mask
+};
 
 struct sl_ctx {
   sl_mesh mesh{};
@@ -169,9 +227,11 @@ struct sl_ctx {
   sl::Basis1D b;
   // fit operators per constraint mask (index = mask & 3 for linear rows) and fit mode
   sl::FitOps fit[4][2];
+  sl_ntab nt[sl::NMAX + 1];              // per node count (the context's n, or every n of a map)
   double* d_tables = nullptr;            // device table buffer
   size_t table_off[4][2][3] = {};        // offsets of Cpinv, S, SCt per mask/mode
   size_t off_xi = 0, off_w = 0, off_lam = 0, off_l0 = 0, off_l1 = 0;
+  size_t off_rules = 0;                  // [NMAX + 1][3][NMAX] xi, lam, w of every node count
   unsigned* d_status = nullptr;
   double* d_partial = nullptr;           // reduction workspace
   double* d_result = nullptr;
@@ -180,6 +240,21 @@ struct sl_ctx {
   double* d_io64 = nullptr;
   double* d_work = nullptr;              // 2D workspace between the two phases
   float* d_ftab = nullptr;               // float tables of the mixed 2D path
+  size_t f_rules = 0;                    // float copy of the rules table
+  // element map: p-adaptive meshes and batches of problems (general 2D kernels)
+  bool mapped = false;
+  int nprob = 1;
+  int64_t nel = 0;                       // elements (all problems)
+  std::vector<uint8_t> ord_host;         // node count per element
+  std::vector<int64_t> off_host;         // value offset per element, then the total
+  std::vector<sl_mesh> prob_mesh;        // meshes of the problems of a batch
+  std::vector<sl::ProbGeom> geo_host;
+  int64_t bucket_start[sl::NMAX + 1] = {}, bucket_count[sl::NMAX + 1] = {};
+  int64_t* d_off = nullptr;
+  uint8_t* d_ord = nullptr;
+  uint16_t* d_prob = nullptr;
+  sl::ProbGeom* d_geo = nullptr;
+  int* d_list = nullptr;                 // element lists of the node-count buckets
   // cached shared operator of the mixed 2D constant-velocity path
   bool m2c_valid = false;
   double m2c_a = 0, m2c_b = 0, m2c_dt = 0;

@@ -151,6 +151,22 @@ def batch_sizes(nprob=64, seed=1):
     return np.random.default_rng(seed).integers(32, 257, nprob)
 
 
+def batch_orders(i, k):
+    """Per-element node counts of problem i of the batched workload (k x k elements)."""
+    return np.random.default_rng(100 + i).integers(3, 16, (k, k)).astype(np.int32) + 1
+
+
+def config4_batch(nprob=64):
+    """The batched rotation workload: nprob independent p-adaptive problems of config 4's kind,
+    side lengths from batch_sizes, node counts from batch_orders."""
+    probs = []
+    for i, k in enumerate(batch_sizes(nprob)):
+        p = config4_rotation(int(k), seed=0)
+        p.orders = batch_orders(i, int(k))
+        probs.append(p)
+    return probs
+
+
 # ----------------------------------------------------------------------------- random states
 
 
