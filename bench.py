@@ -300,7 +300,8 @@ TRAFFIC = {}
 
 def _problem_state(sl, torch, prob, precision):
     """Context and initial state (device doubles) of a workload."""
-    ctx = sl.Context(prob.dim, prob.kx, prob.ky, prob.box, prob.n, prob.basis, precision, prob.bc, prob.ghost)
+    ctx = sl.Context(prob.dim, prob.kx, prob.ky, prob.box, prob.n, prob.basis, precision, prob.bc, prob.ghost,
+                     orders=prob.orders)
     x, y = ctx.node_coords()
     phi = prob.phi0(x) if prob.dim == 1 else prob.phi0(x, y)
     return ctx, torch.tensor(np.ascontiguousarray(phi).ravel(), device="cuda")
@@ -309,7 +310,8 @@ def _problem_state(sl, torch, prob, precision):
 def measure_config(sl, torch, prob, precision, steps, flush, phi=None):
     """Per-step CUDA-event time of one workload on one path (L2 flushed before each step)."""
     ctx, phi0 = _problem_state(sl, torch, prob, precision) if phi is None else (
-        sl.Context(prob.dim, prob.kx, prob.ky, prob.box, prob.n, prob.basis, precision, prob.bc, prob.ghost), phi)
+        sl.Context(prob.dim, prob.kx, prob.ky, prob.box, prob.n, prob.basis, precision, prob.bc, prob.ghost,
+                   orders=prob.orders), phi)
     vel = sl.velocity(prob.velocity.kind, *prob.velocity.p)
     dt = ctx.max_dt(vel, sl_inputs.rule_code(prob))
     opts = sl.options(prob.constraints, prob.rk_order)
@@ -334,6 +336,8 @@ def secondary_configs(sl, torch, flush, quick=False):
     for n in (5, 9, 13, 17):
         plan.append((f"1d_gauss_K2^20_n{n} (config 2)", sl_inputs.config2_1d_gauss(n), [sl.MIXED, sl.FP64], 50))
     plan.append(("2d_const_512x512_n9 (config 3)", sl_inputs.config3_2d_const(), [sl.MIXED, sl.FP64], 10))
+    plan.append(("2d_rotation_256x256_p-adaptive_n4-16 (config 4)", sl_inputs.config4_rotation(), [sl.MIXED, sl.FP64],
+                 10))
     if not quick:
         plan.append(("2d_swirl_2048x2048_n8 (config 5)", sl_inputs.config5_swirl(), [sl.MIXED, sl.FP64], 3))
     for name, prob, precs, steps in plan:
@@ -357,7 +361,56 @@ def secondary_configs(sl, torch, flush, quick=False):
         del outs, phi0
         torch.cuda.empty_cache()
         res.append(entry)
+    res.append(measure_batch(sl, torch, flush, nprob=16 if quick else 64))
     return res
+
+
+def measure_batch(sl, torch, flush, nprob=64, steps=3):
+    """The batched rotation workload: nprob p-adaptive problems (sides 32..256) advanced together,
+    each with its own step (sl_batch_step), mixed precision; one FP64 batch step for the error."""
+    probs = sl_inputs.config4_batch(nprob)
+    entry = {"workload": f"2d_rotation_batch_{nprob}_problems_p-adaptive (config 4 batch)"}
+    outs = {}
+    phi0 = None
+    for prec in (sl.MIXED, sl.FP64):
+        ctxs = [sl.Context(2, p.kx, p.ky, p.box, p.n, p.basis, prec, p.bc, p.ghost, orders=p.orders) for p in probs]
+        batch = sl.Batch(ctxs)
+        vel = sl.velocity(probs[0].velocity.kind, *probs[0].velocity.p)
+        dts = [c.max_dt(vel, sl_inputs.rule_code(p)) for c, p in zip(ctxs, probs)]
+        if phi0 is None:
+            phis = []
+            for c, p in zip(ctxs, probs):
+                x, y = c.node_coords()
+                phis.append(torch.tensor(p.phi0(x, y), device="cuda"))
+            phi0 = torch.cat(phis)
+            del phis
+        opts = sl.options(probs[0].constraints, probs[0].rk_order)
+        a, b = batch.pack(phi0), batch.new_state()
+        key = "mixed" if prec == sl.MIXED else "fp64"
+        batch.batch_step(a, b, vel, [0.0] * nprob, dts, opts)
+        outs[key] = batch.unpack(b)
+        n_steps = steps if prec == sl.MIXED else 1
+        stream = batch.stream
+        times = []
+        for s in range(n_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.batch_step(b, a, vel, [d * (s + 1) for d in dts], dts, opts)
+            e1.record(stream)
+            a, b = b, a
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        per = float(np.mean(times))
+        entry["nodes"] = batch.size
+        entry[key] = {"ms_per_step": per, "node_updates_per_s": batch.size / (per * 1e-3), "steps": n_steps,
+                      "device_status": batch.sync()}
+        del batch, ctxs, a, b
+        torch.cuda.empty_cache()
+    d = outs["mixed"] - outs["fp64"]
+    entry["mixed_vs_fp64_rel_l2_after_1_step"] = float((d.norm() / outs["fp64"].norm()).item())
+    entry["mixed_speedup_over_fp64"] = entry["fp64"]["ms_per_step"] / entry["mixed"]["ms_per_step"]
+    return entry
 
 
 def main():

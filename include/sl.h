@@ -153,6 +153,18 @@ void sl_free(sl_ctx* ctx);
 sl_status sl_step(sl_ctx* ctx, const void* phi_in, void* phi_out, const sl_velocity* vel,
                   double t, double dt, const sl_options* opt);
 
+/* Advance nsteps steps from t0 with a fixed dt (Sec. 4 per step), alternating between two
+ * distinct device state buffers: phi_a holds the initial state; the result is in phi_a when
+ * nsteps is even and in phi_b when it is odd (the other buffer holds the previous step).  The
+ * steps are captured once into a CUDA graph on a stream owned by the context and replayed by
+ * later calls with identical arguments (velocity, t0, dt, nsteps, options, buffers); the graph
+ * is ordered after the work already enqueued on the context's stream, and that stream waits
+ * for it.  Operators are prepared before the capture, so no host-to-device copy is recorded.
+ * A batch runs every problem with the same t0 and dt (see sl_batch_create).  Argument and CFL
+ * errors are reported before anything is enqueued; device errors are sticky bits (sl_sync). */
+sl_status sl_run(sl_ctx* ctx, void* phi_a, void* phi_b, const sl_velocity* vel, double t0, double dt,
+                 int nsteps, const sl_options* opt);
+
 /* Advance nsteps steps from t0 with a fixed dt, starting from and ending in HOST buffers of
  * sl_state_size doubles (node values in state layout, whatever the precision): copies host_in
  * to the device (converting to the state format), steps, converts back and copies the result

@@ -634,6 +634,12 @@ def _periodic_shift(setup, ex, ey, face, nb):
     return (nb[0] - (ex + dx)) * setup.hx, (nb[1] - (ey + dy)) * setup.hy
 
 
+def face_rule_points(n_own, n_nb):
+    """Gauss points of the flux rule on a face between elements of n_own and n_nb nodes (R10: the
+    side with more nodes, so both elements integrate the same points)."""
+    return max(n_own, n_nb)
+
+
 def element_step_2d(setup, phi, ex, ey, o, phihat_cache=None):
     """One DSEM-SL step for element (ex, ey) of a 2D mesh (Sec. 4, two-dimensional scheme).
 
@@ -690,7 +696,7 @@ def element_step_2d(setup, phi, ex, ey, o, phihat_cache=None):
         _, b, c = rk_tableau(o.rk_order)
         for face in range(4):
             nb = _nb_2d(setup, ex, ey, face)
-            nq = n if nb is None else max(n, setup.n_of(*nb))   # R10
+            nq = n if nb is None else face_rule_points(n, setup.n_of(*nb))
             xf, yf, nrm, Wq = _face_points(setup, ex, ey, face, nq)
             for s in range(len(b)):
                 tau = o.t + c[s] * o.dt

@@ -24,7 +24,7 @@ BV_INTERP, BV_BACKTRACK = 0, 1
 RULE_HALF_MIN_SPACING, RULE_PAPER = 0, 1
 ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV = 1, 2, 4
 
-EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
+EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
            "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",
            "sl_integral_noalloc", "sl_batch_create", "sl_batch_step", "sl_batch_offset", "sl_last_error"]
 
@@ -63,6 +63,7 @@ def load_library(path=LIB_PATH):
     lib.sl_step.argtypes = [P, P, P, C.POINTER(SlVelocity), C.c_double, C.c_double, C.POINTER(SlOptions)]
     lib.sl_run_host.argtypes = [P, P, P, C.POINTER(SlVelocity), C.c_double, C.c_double, C.c_int,
                                 C.POINTER(SlOptions)]
+    lib.sl_run.argtypes = [P, P, P, C.POINTER(SlVelocity), C.c_double, C.c_double, C.c_int, C.POINTER(SlOptions)]
     lib.sl_pack.argtypes = [P, P, P]
     lib.sl_unpack.argtypes = [P, P, P]
     lib.sl_state_bytes.argtypes = [P]
@@ -197,6 +198,15 @@ class Context:
         self._state(phi_out, "phi_out")
         self._check(self._lib.sl_step(self._h, _ptr(phi_in), _ptr(phi_out), C.byref(vel), float(t), float(dt),
                                       C.byref(opts)))
+
+    def run(self, phi_a, phi_b, vel, t0, dt, nsteps, opts):
+        """nsteps graph-replayed steps alternating between phi_a (initial state) and phi_b;
+        returns the buffer that holds the result."""
+        self._state(phi_a, "phi_a")
+        self._state(phi_b, "phi_b")
+        self._check(self._lib.sl_run(self._h, _ptr(phi_a), _ptr(phi_b), C.byref(vel), float(t0), float(dt),
+                                     int(nsteps), C.byref(opts)))
+        return phi_a if nsteps % 2 == 0 else phi_b
 
     def run_host(self, host_in, host_out, vel, t0, dt, nsteps, opts):
         """host_in/host_out: CPU float64 tensors (pinned for speed) of node values."""

@@ -334,6 +334,11 @@ void sl_free(sl_ctx* c) {
   cudaFree(c->d_prob);
   cudaFree(c->d_geo);
   cudaFree(c->d_list);
+  cudaFree(c->d_geo_run);
+  if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
+  if (c->run_ev[0]) cudaEventDestroy(c->run_ev[0]);
+  if (c->run_ev[1]) cudaEventDestroy(c->run_ev[1]);
+  if (c->run_stream) cudaStreamDestroy(c->run_stream);
   delete c;
 }
 
@@ -449,7 +454,7 @@ void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, d
     map.off = c->d_off;
     map.ord = c->d_ord;
     map.prob = c->d_prob;
-    map.geo = c->d_geo;
+    map.geo = c->geo_override ? c->geo_override : c->d_geo;
     ts = 4 * NMAX;
   }
   map.tstride = ts;
@@ -495,6 +500,42 @@ void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, d
         launch_step2d_mixed(phase, n, P, X, map, count, (const float*)in, (float*)out, w, c->d_status, c->stream);
       }
     }
+}
+
+// the mixed 2D constant-velocity path (one operator shared by every element)
+bool uses_m2c(const sl_ctx* c, const sl_velocity* vel, const sl_options* opt) {
+  return c->mesh.dim == 2 && c->precision == SL_MIXED && !c->mapped && vel->kind == SL_VEL_CONST &&
+         vel->p[0] != 0.0 && vel->p[1] != 0.0 && opt->fit == SL_FIT_HARD && !(opt->constraints & SL_C_ENERGY) &&
+         opt->bvalue == SL_BV_INTERP && (opt->constraints & 3u);
+}
+
+// build and upload the shared operator unless the cached one matches (velocity, dt, options)
+sl_status ensure_m2c(sl_ctx* c, const sl_velocity* vel, double dt, const sl_options* opt) {
+  if (!c->m2c_valid || c->m2c_a != vel->p[0] || c->m2c_b != vel->p[1] || c->m2c_dt != dt ||
+      c->m2c_cons != opt->constraints || c->m2c_rk != opt->rk_order) {
+    std::string why;
+    if (!build_mixed2d_const(c, vel->p[0], vel->p[1], dt, opt->constraints, opt->rk_order, c->m2c_host, c->m2c, why))
+      return fail(c, SL_EUNSUPPORTED, why);
+    if (c->m2c_host.size() > c->m2c_cap) {
+      cudaFree(c->d_m2c);
+      c->d_m2c = nullptr;
+      c->m2c_cap = 0;
+      if (cudaMalloc(&c->d_m2c, c->m2c_host.size() * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, SL_ENOMEM, "device allocation of the shared operator failed");
+      }
+      c->m2c_cap = c->m2c_host.size();
+    }
+    SL_CUDA(c, cudaMemcpyAsync(c->d_m2c, c->m2c_host.data(), c->m2c_host.size() * sizeof(float),
+                               cudaMemcpyHostToDevice, c->stream));
+    c->m2c_valid = true;
+    c->m2c_a = vel->p[0];
+    c->m2c_b = vel->p[1];
+    c->m2c_dt = dt;
+    c->m2c_cons = opt->constraints;
+    c->m2c_rk = opt->rk_order;
+  }
+  return SL_OK;
 }
 
 sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocity* vel, double t, double dt,
@@ -556,34 +597,10 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
     if (opt->bvalue != SL_BV_INTERP)
       return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
     step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
-  } else if (M.dim == 2 && c->precision == SL_MIXED && !c->mapped && vel->kind == SL_VEL_CONST && vel->p[0] != 0.0 &&
-             vel->p[1] != 0.0 && opt->fit == SL_FIT_HARD && !(opt->constraints & SL_C_ENERGY) &&
-             opt->bvalue == SL_BV_INTERP && (opt->constraints & 3u)) {
+  } else if (uses_m2c(c, vel, opt)) {
     // uniform mesh, constant velocity: one operator shared by all elements
-    if (!c->m2c_valid || c->m2c_a != vel->p[0] || c->m2c_b != vel->p[1] || c->m2c_dt != dt ||
-        c->m2c_cons != opt->constraints || c->m2c_rk != opt->rk_order) {
-      std::string why;
-      if (!build_mixed2d_const(c, vel->p[0], vel->p[1], dt, opt->constraints, opt->rk_order, c->m2c_host, c->m2c, why))
-        return fail(c, SL_EUNSUPPORTED, why);
-      if (c->m2c_host.size() > c->m2c_cap) {
-        cudaFree(c->d_m2c);
-        c->d_m2c = nullptr;
-        c->m2c_cap = 0;
-        if (cudaMalloc(&c->d_m2c, c->m2c_host.size() * sizeof(float)) != cudaSuccess) {
-          cudaGetLastError();
-          return fail(c, SL_ENOMEM, "device allocation of the shared operator failed");
-        }
-        c->m2c_cap = c->m2c_host.size();
-      }
-      SL_CUDA(c, cudaMemcpyAsync(c->d_m2c, c->m2c_host.data(), c->m2c_host.size() * sizeof(float),
-                                 cudaMemcpyHostToDevice, c->stream));
-      c->m2c_valid = true;
-      c->m2c_a = vel->p[0];
-      c->m2c_b = vel->p[1];
-      c->m2c_dt = dt;
-      c->m2c_cons = opt->constraints;
-      c->m2c_rk = opt->rk_order;
-    }
+    sl_status st = ensure_m2c(c, vel, dt, opt);
+    if (st != SL_OK) return st;
     c->m2c.plane = plane_stride(c->nvals);
     launch_step2d_const(c->m2c, c->d_m2c, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream);
   } else if (M.dim == 2 && c->precision == SL_MIXED) {
@@ -640,6 +657,91 @@ sl_status sl_batch_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
   st = set_batch_steps(c, vel, t, dt);
   if (st != SL_OK) return st;
   return step_dispatch(c, phi_in, phi_out, vel, t[0], dt[0], opt);
+}
+
+sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, double t0, double dt, int nsteps,
+                 const sl_options* opt) {
+  if (!c) return SL_EINVAL;
+  if (nsteps < 0) return fail(c, SL_EINVAL, "nsteps must be >= 0");
+  sl_status st = check_step(c, phi_a, phi_b, vel, opt);
+  if (st != SL_OK) return st;
+  if (nsteps == 0) return SL_OK;
+  const bool batch = !c->geo_host.empty();
+  if (batch) {
+    for (int p = 0; p < c->nprob; ++p)
+      if ((st = check_dt(c, c->prob_mesh[p], vel, t0, dt)) != SL_OK) return st;
+  } else if ((st = check_dt(c, c->mesh, vel, t0, dt)) != SL_OK) {
+    return st;
+  }
+  if (!std::isfinite(t0 + nsteps * dt)) return fail(c, SL_EINVAL, "t0 + nsteps dt must be finite");
+  // operators that a step would upload are prepared before (and outside) the capture
+  if (uses_m2c(c, vel, opt) && (st = ensure_m2c(c, vel, dt, opt)) != SL_OK) return st;
+  if (!c->run_stream) {
+    if (cudaStreamCreateWithFlags(&c->run_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->run_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->run_ev[1], cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, SL_ECUDA, std::string("run stream: ") + cudaGetErrorString(cudaGetLastError()));
+  }
+  std::vector<double> key = {(double)vel->kind, t0, dt, (double)nsteps, (double)opt->constraints,
+                             (double)opt->rk_order, (double)opt->fit, (double)opt->bvalue, opt->picard_rtol,
+                             (double)opt->picard_cap, (double)(uintptr_t)phi_a, (double)(uintptr_t)phi_b};
+  for (int i = 0; i < 6; ++i) key.push_back(vel->p[i]);
+  if (!c->run_valid || key != c->run_key) {
+    if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
+    c->run_exec = nullptr;
+    c->run_valid = false;
+    if (batch) {                             // every step's times and steps, uploaded once
+      const size_t need = (size_t)nsteps * c->nprob;
+      if (need > c->geo_run_cap) {
+        cudaFree(c->d_geo_run);
+        c->d_geo_run = nullptr;
+        c->geo_run_cap = 0;
+        if (cudaMalloc(&c->d_geo_run, need * sizeof(ProbGeom)) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(c, SL_ENOMEM, "device allocation of the run geometry failed");
+        }
+        c->geo_run_cap = need;
+      }
+      std::vector<ProbGeom> g(need);
+      for (int s = 0; s < nsteps; ++s)
+        for (int p = 0; p < c->nprob; ++p) {
+          g[(size_t)s * c->nprob + p] = c->geo_host[p];
+          g[(size_t)s * c->nprob + p].t = t0 + s * dt;
+          g[(size_t)s * c->nprob + p].dt = dt;
+        }
+      SL_CUDA(c, cudaMemcpy(c->d_geo_run, g.data(), need * sizeof(ProbGeom), cudaMemcpyHostToDevice));
+    }
+    const cudaStream_t user = c->stream;
+    c->stream = c->run_stream;
+    SL_CUDA(c, cudaStreamBeginCapture(c->run_stream, cudaStreamCaptureModeThreadLocal));
+    void* a = phi_a;
+    void* b = phi_b;
+    for (int s = 0; s < nsteps && st == SL_OK; ++s) {
+      if (batch) c->geo_override = c->d_geo_run + (size_t)s * c->nprob;
+      st = step_dispatch(c, a, b, vel, t0 + s * dt, dt, opt);
+      std::swap(a, b);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(c->run_stream, &graph);
+    c->stream = user;
+    c->geo_override = nullptr;
+    if (st == SL_OK && ce != cudaSuccess) st = fail(c, SL_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    if (st == SL_OK && cudaGraphInstantiate(&c->run_exec, graph, 0) != cudaSuccess) {
+      c->run_exec = nullptr;
+      st = fail(c, SL_ECUDA, std::string("graph instantiation: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != SL_OK) return st;
+    c->run_key = key;
+    c->run_valid = true;
+  }
+  // the graph runs after the work already on the context's stream, and the stream waits for it
+  SL_CUDA(c, cudaEventRecord(c->run_ev[0], c->stream));
+  SL_CUDA(c, cudaStreamWaitEvent(c->run_stream, c->run_ev[0], 0));
+  SL_CUDA(c, cudaGraphLaunch(c->run_exec, c->run_stream));
+  SL_CUDA(c, cudaEventRecord(c->run_ev[1], c->run_stream));
+  SL_CUDA(c, cudaStreamWaitEvent(c->stream, c->run_ev[1], 0));
+  return SL_OK;
 }
 
 sl_status sl_run_host(sl_ctx* c, const double* host_in, double* host_out, const sl_velocity* vel, double t0,

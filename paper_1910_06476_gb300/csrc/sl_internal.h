@@ -255,6 +255,15 @@ struct sl_ctx {
   uint16_t* d_prob = nullptr;
   sl::ProbGeom* d_geo = nullptr;
   int* d_list = nullptr;                 // element lists of the node-count buckets
+  // sl_run: steps captured into a CUDA graph on an internal stream, kept for identical calls
+  cudaStream_t run_stream = nullptr;
+  cudaEvent_t run_ev[2] = {};
+  cudaGraphExec_t run_exec = nullptr;
+  bool run_valid = false;
+  std::vector<double> run_key;
+  sl::ProbGeom* d_geo_run = nullptr;     // per-step geometry of a batch run, [nsteps][nprob]
+  size_t geo_run_cap = 0;
+  const sl::ProbGeom* geo_override = nullptr;
   // cached shared operator of the mixed 2D constant-velocity path
   bool m2c_valid = false;
   double m2c_a = 0, m2c_b = 0, m2c_dt = 0;
