@@ -288,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
             "fp64_per_element": fp64,
             "device_status": status}
     if not args.no_configs:
-        line["configs"] = secondary_configs(sl, torch, flush, quick=args.quick_configs)
+        line["configs"] = secondary_configs(sl, torch, flush, full=args.all_configs)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n, seconds=args.ref_seconds)
     print(json.dumps(line), flush=True)
@@ -329,8 +329,9 @@ def measure_config(sl, torch, prob, precision, steps, flush, phi=None):
         ctx, vel, dt, opts)
 
 
-def secondary_configs(sl, torch, flush, quick=False):
-    """Every configuration of the measurement plan on both paths, outside the headline timed region."""
+def secondary_configs(sl, torch, flush, full=False):
+    """The other configurations of the measurement plan on both paths, outside the headline timed
+    region (the 2048^2 swirl and the 64-problem batch only with full=True)."""
     res = []
     plan = [("1d_sine_K16_n9 (config 1)", sl_inputs.config1_1d_sine(), [sl.FP64], 200)]
     for n in (5, 9, 13, 17):
@@ -338,7 +339,7 @@ def secondary_configs(sl, torch, flush, quick=False):
     plan.append(("2d_const_512x512_n9 (config 3)", sl_inputs.config3_2d_const(), [sl.MIXED, sl.FP64], 10))
     plan.append(("2d_rotation_256x256_p-adaptive_n4-16 (config 4)", sl_inputs.config4_rotation(), [sl.MIXED, sl.FP64],
                  10))
-    if not quick:
+    if full:
         plan.append(("2d_swirl_2048x2048_n8 (config 5)", sl_inputs.config5_swirl(), [sl.MIXED, sl.FP64], 3))
     for name, prob, precs, steps in plan:
         entry = {"workload": name, "nodes": None}
@@ -354,6 +355,26 @@ def secondary_configs(sl, torch, flush, quick=False):
             ctx.step(a, b, vel, 0.0, dt, opts)
             outs[key] = ctx.unpack(b)
             del ctx, a, b
+        if prob.kx * prob.ky <= 64:
+            # a launch-bound workload: the same steps replayed from one CUDA graph (sl_run); the
+            # whole state (a few KB) stays in L2 either way, so no flush between steps
+            prec = precs[0]
+            ctx = sl.Context(prob.dim, prob.kx, prob.ky, prob.box, prob.n, prob.basis, prec, prob.bc, prob.ghost)
+            vel = sl.velocity(prob.velocity.kind, *prob.velocity.p)
+            dt = ctx.max_dt(vel, sl_inputs.rule_code(prob))
+            opts = sl.options(prob.constraints, prob.rk_order)
+            a, b = ctx.pack(phi0), ctx.new_state()
+            ctx.run(a, b, vel, 0.0, dt, steps, opts)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            ctx.run(a, b, vel, 0.0, dt, steps, opts)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            per = e0.elapsed_time(e1) / steps
+            entry["graph_replay"] = {"ms_per_step": per, "node_updates_per_s": entry["nodes"] / (per * 1e-3),
+                                     "steps": steps, "api": "sl_run", "device_status": ctx.sync()}
+            del ctx, a, b
         if "mixed" in outs and "fp64" in outs:
             d = outs["mixed"] - outs["fp64"]
             entry["mixed_vs_fp64_rel_l2_after_1_step"] = float((d.norm() / outs["fp64"].norm()).item())
@@ -361,7 +382,7 @@ def secondary_configs(sl, torch, flush, quick=False):
         del outs, phi0
         torch.cuda.empty_cache()
         res.append(entry)
-    res.append(measure_batch(sl, torch, flush, nprob=16 if quick else 64))
+    res.append(measure_batch(sl, torch, flush, nprob=64 if full else 16))
     return res
 
 
@@ -426,7 +447,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-element comparison")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-configs", action="store_true", help="skip the other configurations")
-    ap.add_argument("--quick-configs", action="store_true", help="other configurations without the 2048^2 one")
+    ap.add_argument("--all-configs", action="store_true",
+                    help="add the 2048^2 swirl and the 64-problem batch to the other configurations")
+    ap.add_argument("--quick-configs", action="store_true", help="(default) other configurations, smaller set")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

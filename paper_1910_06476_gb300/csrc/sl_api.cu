@@ -3,8 +3,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 
 #include "sl_internal.h"
 
@@ -79,19 +83,44 @@ struct TableBufs {
   }
 };
 
-// basis and fit operators of node count n, appended to the table buffers (throws on failure)
-void build_ntab(sl_ntab& t, int n, int basis, int dim, bool mixed2d, TableBufs& B) {
-  t.present = true;
-  t.b = make_basis(n, basis);
+// Basis and fit operators of one (node count, basis, dimension): built once per process (they
+// cost up to about a second each at n = 17) and shared by every context.
+struct HostOps {
+  Basis1D b;
+  FitOps fit[4][2];
+};
+
+std::shared_ptr<const HostOps> host_ops(int n, int basis, int dim) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, std::shared_ptr<const HostOps>> cache;
+  const auto key = std::make_tuple(n, basis, dim);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  auto h = std::make_shared<HostOps>();
+  h->b = make_basis(n, basis);
   for (unsigned mask = 0; mask < 4; ++mask)
     for (int soft = 0; soft < 2; ++soft) {
       if (dim == 1) {
-        t.fit[mask][soft] = make_fit_1d(t.b, mask);
-        finish_fit(t.fit[mask][soft], soft != 0);
+        h->fit[mask][soft] = make_fit_1d(h->b, mask);
+        finish_fit(h->fit[mask][soft], soft != 0);
       } else {
-        t.fit[mask][soft] = make_fit_2d(t.b, mask, soft != 0);
+        h->fit[mask][soft] = make_fit_2d(h->b, mask, soft != 0);
       }
     }
+  std::lock_guard<std::mutex> lock(mu);
+  return cache.emplace(key, std::move(h)).first->second;
+}
+
+// basis and fit operators of node count n, appended to the table buffers (throws on failure)
+void build_ntab(sl_ntab& t, int n, int basis, int dim, bool mixed2d, TableBufs& B) {
+  t.present = true;
+  const std::shared_ptr<const HostOps> h = host_ops(n, basis, dim);
+  t.b = h->b;
+  for (unsigned mask = 0; mask < 4; ++mask)
+    for (int soft = 0; soft < 2; ++soft) t.fit[mask][soft] = h->fit[mask][soft];
   t.off_xi = B.put(t.b.xi, NMAX);
   t.off_w = B.put(t.b.w, NMAX);
   t.off_lam = B.put(t.b.lam, NMAX);
