@@ -25,7 +25,8 @@
  *     many floats "lo" at float offset P = sl_state_size rounded up to a multiple of 64 (so
  *     both planes start 256-byte aligned); the node value is hi + lo (about 48 significant
  *     bits).  sl_pack and sl_unpack convert from and to doubles.  A state buffer has
- *     sl_state_bytes bytes (8 per node, plus the padding of the mixed format).
+ *     sl_state_bytes bytes (8 per node, plus the padding of the mixed format) and starts on a
+ *     16-byte boundary (state is moved with 16-byte vectors and bulk copies).
  *   - Pointers documented as "host" are host memory; everything else is device memory.
  *   - The library owns its tables, operators and workspace (allocated in sl_init and freed in
  *     sl_free).  All device work is enqueued on the stream given to sl_init; no call
@@ -101,7 +102,9 @@ enum { SL_RULE_HALF_MIN_SPACING = 0, SL_RULE_PAPER = 1 };
 enum {
   SL_ST_NONFINITE = 1u,      /* a non-finite value was written                          */
   SL_ST_PICARD_NOCONV = 2u,  /* the energy iteration hit its cap or was infeasible      */
-  SL_ST_SOLVE_NOCONV = 4u    /* the 2D collocation iteration hit its cap                */
+  SL_ST_SOLVE_NOCONV = 4u,   /* the 2D collocation iteration hit its cap                */
+  SL_ST_TIMEOUT = 8u         /* a bounded wait for an asynchronous copy gave up (the step
+                                left its output incomplete)                             */
 };
 
 typedef struct {

@@ -22,7 +22,7 @@ C_BOUNDARY, C_MASS, C_ENERGY = 1, 2, 4
 FIT_HARD, FIT_SOFT = 0, 1
 BV_INTERP, BV_BACKTRACK = 0, 1
 RULE_HALF_MIN_SPACING, RULE_PAPER = 0, 1
-ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV = 1, 2, 4
+ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV, ST_TIMEOUT = 1, 2, 4, 8
 
 EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
            "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",

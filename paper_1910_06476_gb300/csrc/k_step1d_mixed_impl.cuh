@@ -13,14 +13,22 @@
 //     from increments only, so that the decision to apply it is free of float cancellation;
 //   - the result is written back exactly as ref + psi by TwoSum (Knuth), hi = fl(ref + psi),
 //     lo = (ref + psi) - hi.
-// The tile (and its upwind halo element) is staged through shared memory with coalesced loads
-// and stores; the kernel reads 8 and writes 8 bytes per node from HBM.
+// The kernel is persistent: a CTA advances tiles of TILE elements, one thread per element.  A
+// tile's rows (its elements and the upwind halo element) are one contiguous run of each plane;
+// one thread moves both runs into shared memory with bulk asynchronous copies (TMA) that complete
+// on an mbarrier, into one of two stages, so the next tile's load overlaps this tile's
+// arithmetic.  Results are written back into the stage and stored with bulk copies.  The kernel
+// reads 8 and writes 8 bytes per node from HBM.  Every wait on a copy is bounded: on a timeout
+// the CTA stops, reports SL_ST_TIMEOUT, and drains its stores.
+#include <algorithm>
+
 #include "sl_internal.h"
 
 namespace sl {
 namespace k1m {
 
-constexpr int TILE = 256;                  // elements (threads) per CTA
+constexpr int TILE = 256;                  // elements (threads) per tile
+constexpr int WAIT_LIMIT = 1 << 22;        // polls of an mbarrier before a wait gives up
 
 __device__ __forceinline__ int wrap_elem(int e, int K, bool periodic) {
   if (e >= 0 && e < K) return e;
@@ -29,226 +37,333 @@ __device__ __forceinline__ int wrap_elem(int e, int K, bool periodic) {
   return e < 0 ? e + K : e;
 }
 
+// ---- bulk asynchronous copies (PTX cp.async.bulk) and mbarriers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// global -> shared, completion counted in bytes on bar; addresses and size multiples of 16 bytes
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// shared -> global in the thread's bulk group; addresses and size multiples of 16 bytes
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// this thread's shared-memory writes become visible to later bulk copies (async proxy)
+__device__ __forceinline__ void fence_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// floats of one plane of one stage: TILE + 1 rows, up to 3 floats of alignment shift, and the
+// rounding of the copied run to 16 bytes at both ends
 template <int NN>
-__global__ void __launch_bounds__(TILE) k_step1d_mixed(const __grid_constant__ Mixed1DParams P,
-                                                       const float* __restrict__ in, float* __restrict__ out,
-                                                       unsigned* status) {
-  constexpr int SH = 4;                     // row r of the tile lives at s[SH + r * NN + i]
-  constexpr int SMEM = (TILE + 1) * NN + 16;
-  __shared__ __align__(16) float shi[SMEM];
-  __shared__ __align__(16) float slo[SMEM];
+__host__ __device__ constexpr int stage_floats() { return ((TILE + 1) * NN + 16 + 3) & ~3; }
+
+// Where tile t's rows sit: rows r in [r_lo, r_hi) are elements first + r inside [0, K), one
+// contiguous run of floats [g0, g1) of each plane, copied as the 16-byte-aligned window [a0, a1)
+// to shared offset sbase; row r starts at shared offset sh + r NN.  sh in [0, 4) makes sbase a
+// multiple of 4 floats.
+struct TileGeo {
+  int e0, first, r_lo, r_hi, sh, sbase, nvec;
+  int64_t a0;
+};
+
+template <int NN>
+__device__ __forceinline__ TileGeo tile_geo(const Mixed1DParams& P, int t) {
+  TileGeo g;
+  g.e0 = t * TILE;
+  g.first = P.left_up ? g.e0 - 1 : g.e0;
+  g.r_lo = max(0, -g.first);
+  g.r_hi = min(TILE + 1, P.K - g.first);
+  const int64_t g0 = (int64_t)(g.first + g.r_lo) * NN, g1 = (int64_t)(g.first + g.r_hi) * NN;
+  g.a0 = g0 & ~int64_t(3);
+  const int64_t a1 = (g1 + 3) & ~int64_t(3);   // within the plane: planes are padded to 64 floats
+  const int d = (int)(g0 - g.a0);
+  g.sh = (d - g.r_lo * NN) & 3;
+  g.sbase = g.sh + g.r_lo * NN - d;
+  g.nvec = (int)((a1 - g.a0) >> 2);
+  return g;
+}
+
+// One element: rows own and up of the staged tile (shi, slo); writes res = phi^{n+1} - ref.
+// Returns false when the energy iteration did not converge (the linear solution is kept).
+template <int NN>
+__device__ __forceinline__ bool element_step(const Mixed1DParams& P, const float* shi, const float* slo, int own,
+                                             int up, bool has_up, float& ref, float (&res)[NN]) {
+  bool ok = true;
+  ref = shi[own];
+  float ps[NN], pu[NN];
+#pragma unroll
+  for (int i = 0; i < NN; ++i) ps[i] = (shi[own + i] - ref) + slo[own + i];
+  if (has_up) {
+#pragma unroll
+    for (int i = 0; i < NN; ++i) pu[i] = (shi[up + i] - ref) + slo[up + i];
+  } else {
+    const float g = (float)(P.ghost - (double)ref);   // ghost value at the inflow domain face
+#pragma unroll
+    for (int i = 0; i < NN; ++i) pu[i] = g;
+  }
+  // shared linear operator
+  float pl[NN];
+#pragma unroll
+  for (int j = 0; j < NN; ++j) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < NN; ++i) acc = fmaf(P.Gs[j * NN + i], ps[i], acc);
+#pragma unroll
+    for (int i = 0; i < NN; ++i) acc = fmaf(P.Gu[j * NN + i], pu[i], acc);
+    pl[j] = acc;
+  }
+#pragma unroll
+  for (int j = 0; j < NN; ++j) res[j] = pl[j];
+
+  if (P.energy_on) {
+    // The energy iteration is covariant under phi -> c phi (gamma, alpha, beta scale by c^2, q by
+    // c, s is invariant), so it runs on values scaled by a power of two to order one; elements
+    // whose values lie below the normal float range carry no energy correction.
+    float smax = fabsf(ref);
+#pragma unroll
+    for (int i = 0; i < NN; ++i) smax = fmaxf(smax, fmaxf(fabsf(ps[i]), fabsf(pu[i])));
+    if (smax >= 1e-30f) {
+      int ex;
+      frexpf(smax, &ex);
+      const float sc = ldexpf(1.0f, -ex), usc = ldexpf(1.0f, ex);
+      const float rf = ref * sc;
+      float qs[NN], qu[NN], ql[NN];
+#pragma unroll
+      for (int i = 0; i < NN; ++i) { qs[i] = ps[i] * sc; qu[i] = pu[i] * sc; ql[i] = pl[i] * sc; }
+      // energy mismatch from increments: variance part, plus 2 ref x mass residual when the mass
+      // row is not enforced (with it, that bracket vanishes identically)
+      float gv = 0.0f, gm = 0.0f, escale = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NN; ++i) {
+        gv = fmaf(P.w[i], (ql[i] - qs[i]) * (ql[i] + qs[i]), gv);
+        gm = fmaf(P.w[i], ql[i] - qs[i], gm);
+        const float phv = rf + qs[i];
+        escale = fmaf(P.w[i], phv * phv, escale);
+      }
+      for (int s = 0; s < P.nst; ++s) {
+        float es = 0.0f, eu = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NN; ++i) { es = fmaf(P.E[s][i], qs[i], es); eu = fmaf(P.E[s][i], qu[i], eu); }
+        gv = fmaf(P.lam * P.fb[s], es * es - eu * eu, gv);
+        gm = fmaf(P.lam * P.fb[s], es - eu, gm);
+      }
+      const float gamma = P.mass_on ? gv : fmaf(2.0f * rf, gm, gv);
+      if (fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {
+        float pmax = 0.0f;
+#pragma unroll
+        for (int i = 0; i < NN; ++i) pmax = fmaxf(pmax, fabsf(ql[i]));
+        const float tol = fmaxf(P.picard_rtol * fabsf(rf), 2.4e-7f * pmax) + 1e-30f;
+        float cur[NN];
+#pragma unroll
+        for (int i = 0; i < NN; ++i) cur[i] = ql[i];
+        bool conv = false, feasible = true;
+        for (int it = 0; it < P.picard_cap; ++it) {
+          float av[NN], q[NN];
+#pragma unroll
+          for (int i = 0; i < NN; ++i) av[i] = P.w[i] * (P.mass_on ? cur[i] : rf + cur[i]);
+          float ca[MMAX1D];
+          for (int k = 0; k < P.m; ++k) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NN; ++i) acc = fmaf(P.C[k * NN + i], av[i], acc);
+            ca[k] = acc;
+          }
+#pragma unroll
+          for (int j = 0; j < NN; ++j) {
+            float acc = av[j];
+            for (int k = 0; k < P.m; ++k) acc = fmaf(-P.Cp[j * P.m + k], ca[k], acc);
+            q[j] = acc;
+          }
+          float alpha = 0.0f, beta = 0.0f, wq = 0.0f;
+#pragma unroll
+          for (int i = 0; i < NN; ++i) {
+            alpha = fmaf(P.w[i] * ql[i], q[i], alpha);
+            beta = fmaf(P.w[i] * q[i], q[i], beta);
+            wq = fmaf(P.w[i], q[i], wq);
+          }
+          if (!P.mass_on) alpha = fmaf(rf, wq, alpha);
+          float s;
+          if (beta <= 0.0f) { s = 0.0f; feasible = gamma <= 0.0f; }
+          else {
+            const float disc = alpha * alpha - beta * gamma;
+            if (disc < 0.0f) { s = -alpha / beta; feasible = false; }
+            else {
+              const float root = sqrtf(disc);
+              const float den = alpha + (alpha >= 0.0f ? root : -root);
+              s = den == 0.0f ? 0.0f : -gamma / den;
+              feasible = true;
+            }
+          }
+          float delta = 0.0f;
+#pragma unroll
+          for (int i = 0; i < NN; ++i) {
+            const float nv = fmaf(s, q[i], ql[i]);
+            delta = fmaxf(delta, fabsf(nv - cur[i]));
+            cur[i] = nv;
+          }
+          if (delta <= tol) { conv = feasible; break; }
+        }
+        if (conv) {
+#pragma unroll
+          for (int i = 0; i < NN; ++i) res[i] = cur[i] * usc;
+        }                                   // else: keep the linear-constraint solution
+        ok = conv;
+      }
+    }
+  }
+  return ok;
+}
+
+template <int NN>
+__global__ void __launch_bounds__(TILE, NN <= 11 ? 3 : 2)
+    k_step1d_mixed(const __grid_constant__ Mixed1DParams P, const float* __restrict__ in, float* __restrict__ out,
+                   unsigned* status) {
+  constexpr int SF = stage_floats<NN>();
+  extern __shared__ __align__(16) float sm[];     // [stage][hi | lo][SF]
+  __shared__ __align__(8) uint64_t bar[2];
   const int tid = threadIdx.x;
   const int K = P.K;
-  const int64_t plane = P.plane;            // float offset of the lo plane (multiple of 64)
-  const int e0 = blockIdx.x * TILE;
-  // tile rows: left upwind -> elements [e0-1, e0+TILE), right upwind -> [e0, e0+TILE]
-  const int first = P.left_up ? e0 - 1 : e0;
-  // rows whose elements lie in [0, K) are contiguous in memory: one aligned 16-byte window
-  const int r_lo = max(0, -first), r_hi = min(TILE + 1, K - first);
-  {
-    const int64_t g0 = (int64_t)(first + r_lo) * NN, g1 = (int64_t)(first + r_hi) * NN;
-    const int64_t a0 = g0 & ~int64_t(3), a1 = (g1 + 3) & ~int64_t(3);   // a1 <= plane: padded
-    const int sbase = SH + r_lo * NN - (int)(g0 - a0);
-    const int nvec = (int)((a1 - a0) >> 2);
-    const float4* ih = reinterpret_cast<const float4*>(in + a0);
-    const float4* il = reinterpret_cast<const float4*>(in + plane + a0);
-    constexpr int VPT = ((TILE + 1) * NN + 8 + 4 * TILE - 1) / (4 * TILE);   // vectors per thread
-    float4 vh[VPT], vl[VPT];
-#pragma unroll
-    for (int k = 0; k < VPT; ++k) {          // issue every load before the first shared store
-      const int v = tid + k * TILE;
-      if (v < nvec) { vh[k] = __ldg(ih + v); vl[k] = __ldg(il + v); }
+  const int64_t plane = P.plane;                  // float offset of the lo plane (multiple of 64)
+  const int ntiles = (K + TILE - 1) / TILE;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // thread 0: both planes of tile t into stage st
+  auto issue = [&](int t, int st) {
+    const TileGeo g = tile_geo<NN>(P, t);
+    float* hi = sm + st * 2 * SF;
+    const unsigned bytes = (unsigned)g.nvec * 16u;
+    mbar_expect_tx(&bar[st], 2u * bytes);
+    bulk_load(hi + g.sbase, in + g.a0, bytes, &bar[st]);
+    bulk_load(hi + SF + g.sbase, in + plane + g.a0, bytes, &bar[st]);
+  };
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  unsigned parity = 0;                            // bit st: phase parity awaited on stage st
+  unsigned bits = 0;
+  int st = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, st ^= 1) {
+    // prefetch the next tile into the other stage once the stores that read it are done
+    const int tn = t + (int)gridDim.x;
+    if (tid == 0 && tn < ntiles) {
+      bulk_wait_read_all();
+      issue(tn, st ^ 1);
     }
+    bool arrived = false;
+    for (int it = 0; it < WAIT_LIMIT && !arrived; ++it) arrived = mbar_try_wait(&bar[st], (parity >> st) & 1u);
+    parity ^= 1u << st;
+    if (__syncthreads_or(!arrived)) {             // every thread leaves together
+      bits |= SL_ST_TIMEOUT;
+      break;
+    }
+    const TileGeo g = tile_geo<NN>(P, t);
+    float* shi = sm + st * 2 * SF;
+    float* slo = shi + SF;
+    // the one halo row outside [0, K): periodic wrap, or zero at an inflow face (unused there)
+    const int hrow = P.left_up ? 0 : g.r_hi;
+    const bool hfix = P.left_up ? (g.r_lo == 1) : (g.r_hi <= TILE);
+    if (hfix && tid < NN) {
+      const int eh = wrap_elem(g.first + hrow, K, P.periodic != 0);
+      shi[g.sh + hrow * NN + tid] = eh >= 0 ? in[(int64_t)eh * NN + tid] : 0.0f;
+      slo[g.sh + hrow * NN + tid] = eh >= 0 ? in[plane + (int64_t)eh * NN + tid] : 0.0f;
+    }
+    __syncthreads();
+    const int e = g.e0 + tid;
+    const bool active = e < K;
+    float res[NN];
+    float ref = 0.0f;
+    if (active) {
+      const int own = g.sh + (P.left_up ? tid + 1 : tid) * NN;
+      const int up = g.sh + (P.left_up ? tid : tid + 1) * NN;
+      const bool has_up = wrap_elem(P.left_up ? e - 1 : e + 1, K, P.periodic != 0) >= 0;
+      if (!element_step<NN>(P, shi, slo, own, up, has_up, ref, res)) bits |= SL_ST_PICARD_NOCONV;
+    }
+    __syncthreads();                              // the stage's rows are rewritten below
+    if (active) {
+      bool finite = true;
 #pragma unroll
-    for (int k = 0; k < VPT; ++k) {
-      const int v = tid + k * TILE;
-      if (v < nvec) {
-        float* dh = shi + sbase + 4 * v;
-        float* dl = slo + sbase + 4 * v;
-        dh[0] = vh[k].x; dh[1] = vh[k].y; dh[2] = vh[k].z; dh[3] = vh[k].w;
-        dl[0] = vl[k].x; dl[1] = vl[k].y; dl[2] = vl[k].z; dl[3] = vl[k].w;
+      for (int j = 0; j < NN; ++j) {
+        // TwoSum: hi + lo == ref + res exactly
+        const float s = ref + res[j];
+        const float bb = s - ref;
+        const float err = (ref - (s - bb)) + (res[j] - bb);
+        shi[tid * NN + j] = s;
+        slo[tid * NN + j] = err;
+        finite = finite && isfinite(s);
       }
+      if (!finite) bits |= SL_ST_NONFINITE;
+      fence_to_async();
     }
-  }
-  // the one halo row that can fall outside [0, K): periodic wrap (or none at an inflow face)
-  const int hrow = P.left_up ? 0 : r_hi;
-  const bool hfix = P.left_up ? (r_lo == 1) : (r_hi <= TILE);
-  __syncthreads();
-  if (hfix && tid < NN) {
-    const int eh = wrap_elem(first + hrow, K, P.periodic != 0);
-    shi[SH + hrow * NN + tid] = eh >= 0 ? in[(int64_t)eh * NN + tid] : 0.0f;
-    slo[SH + hrow * NN + tid] = eh >= 0 ? in[plane + (int64_t)eh * NN + tid] : 0.0f;
-  }
-  __syncthreads();
-
-  const int e = e0 + tid;
-  const bool active = e < K;
-  const int own = SH + (P.left_up ? tid + 1 : tid) * NN;
-  const int up = SH + (P.left_up ? tid : tid + 1) * NN;
-  const int eup = wrap_elem(P.left_up ? e - 1 : e + 1, K, P.periodic != 0);
-  float res[NN];
-  float ref = 0.0f;
-  bool ok = true;
-  if (active) {
-    ref = shi[own];
-    float ps[NN], pu[NN];
-#pragma unroll
-    for (int i = 0; i < NN; ++i) ps[i] = (shi[own + i] - ref) + slo[own + i];
-    if (eup >= 0) {
-#pragma unroll
-      for (int i = 0; i < NN; ++i) pu[i] = (shi[up + i] - ref) + slo[up + i];
-    } else {
-      const float g = (float)(P.ghost - (double)ref);   // ghost value at the inflow domain face
-#pragma unroll
-      for (int i = 0; i < NN; ++i) pu[i] = g;
+    __syncthreads();
+    // the tile's own elements are one run starting at e0 NN (a multiple of 4 floats)
+    const int nout = min(TILE, K - g.e0) * NN, nv = nout >> 2;
+    if (tid == 0 && nv > 0) {
+      bulk_store(out + (int64_t)g.e0 * NN, shi, (unsigned)nv * 16u);
+      bulk_store(out + plane + (int64_t)g.e0 * NN, slo, (unsigned)nv * 16u);
+      bulk_commit();
     }
-    // shared linear operator
-    float pl[NN];
-#pragma unroll
-    for (int j = 0; j < NN; ++j) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int i = 0; i < NN; ++i) acc = fmaf(P.Gs[j * NN + i], ps[i], acc);
-#pragma unroll
-      for (int i = 0; i < NN; ++i) acc = fmaf(P.Gu[j * NN + i], pu[i], acc);
-      pl[j] = acc;
+    for (int idx = 4 * nv + tid; idx < nout; idx += TILE) {
+      out[(int64_t)g.e0 * NN + idx] = shi[idx];
+      out[plane + (int64_t)g.e0 * NN + idx] = slo[idx];
     }
-#pragma unroll
-    for (int j = 0; j < NN; ++j) res[j] = pl[j];
-
-    if (P.energy_on) {
-      // The energy iteration is covariant under phi -> c phi (gamma, alpha, beta scale by c^2, q by
-      // c, s is invariant), so it runs on values scaled by a power of two to order one; elements
-      // whose values lie below the normal float range carry no energy correction.
-      float smax = fabsf(ref);
-#pragma unroll
-      for (int i = 0; i < NN; ++i) smax = fmaxf(smax, fmaxf(fabsf(ps[i]), fabsf(pu[i])));
-      if (smax >= 1e-30f) {
-        int ex;
-        frexpf(smax, &ex);
-        const float sc = ldexpf(1.0f, -ex), usc = ldexpf(1.0f, ex);
-        const float rf = ref * sc;
-        float qs[NN], qu[NN], ql[NN];
-#pragma unroll
-        for (int i = 0; i < NN; ++i) { qs[i] = ps[i] * sc; qu[i] = pu[i] * sc; ql[i] = pl[i] * sc; }
-        // energy mismatch from increments: variance part, plus 2 ref x mass residual when the mass
-        // row is not enforced (with it, that bracket vanishes identically)
-        float gv = 0.0f, gm = 0.0f, escale = 0.0f;
-#pragma unroll
-        for (int i = 0; i < NN; ++i) {
-          gv = fmaf(P.w[i], (ql[i] - qs[i]) * (ql[i] + qs[i]), gv);
-          gm = fmaf(P.w[i], ql[i] - qs[i], gm);
-          const float phv = rf + qs[i];
-          escale = fmaf(P.w[i], phv * phv, escale);
-        }
-        for (int s = 0; s < P.nst; ++s) {
-          float es = 0.0f, eu = 0.0f;
-#pragma unroll
-          for (int i = 0; i < NN; ++i) { es = fmaf(P.E[s][i], qs[i], es); eu = fmaf(P.E[s][i], qu[i], eu); }
-          gv = fmaf(P.lam * P.fb[s], es * es - eu * eu, gv);
-          gm = fmaf(P.lam * P.fb[s], es - eu, gm);
-        }
-        const float gamma = P.mass_on ? gv : fmaf(2.0f * rf, gm, gv);
-        if (fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {
-          float pmax = 0.0f;
-#pragma unroll
-          for (int i = 0; i < NN; ++i) pmax = fmaxf(pmax, fabsf(ql[i]));
-          const float tol = fmaxf(P.picard_rtol * fabsf(rf), 2.4e-7f * pmax) + 1e-30f;
-          float cur[NN];
-#pragma unroll
-          for (int i = 0; i < NN; ++i) cur[i] = ql[i];
-          bool conv = false, feasible = true;
-          for (int it = 0; it < P.picard_cap; ++it) {
-            float av[NN], q[NN];
-#pragma unroll
-            for (int i = 0; i < NN; ++i) av[i] = P.w[i] * (P.mass_on ? cur[i] : rf + cur[i]);
-            float ca[MMAX1D];
-            for (int k = 0; k < P.m; ++k) {
-              float acc = 0.0f;
-#pragma unroll
-              for (int i = 0; i < NN; ++i) acc = fmaf(P.C[k * NN + i], av[i], acc);
-              ca[k] = acc;
-            }
-#pragma unroll
-            for (int j = 0; j < NN; ++j) {
-              float acc = av[j];
-              for (int k = 0; k < P.m; ++k) acc = fmaf(-P.Cp[j * P.m + k], ca[k], acc);
-              q[j] = acc;
-            }
-            float alpha = 0.0f, beta = 0.0f, wq = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NN; ++i) {
-              alpha = fmaf(P.w[i] * ql[i], q[i], alpha);
-              beta = fmaf(P.w[i] * q[i], q[i], beta);
-              wq = fmaf(P.w[i], q[i], wq);
-            }
-            if (!P.mass_on) alpha = fmaf(rf, wq, alpha);
-            float s;
-            if (beta <= 0.0f) { s = 0.0f; feasible = gamma <= 0.0f; }
-            else {
-              const float disc = alpha * alpha - beta * gamma;
-              if (disc < 0.0f) { s = -alpha / beta; feasible = false; }
-              else {
-                const float root = sqrtf(disc);
-                const float den = alpha + (alpha >= 0.0f ? root : -root);
-                s = den == 0.0f ? 0.0f : -gamma / den;
-                feasible = true;
-              }
-            }
-            float delta = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NN; ++i) {
-              const float nv = fmaf(s, q[i], ql[i]);
-              delta = fmaxf(delta, fabsf(nv - cur[i]));
-              cur[i] = nv;
-            }
-            if (delta <= tol) { conv = feasible; break; }
-          }
-          if (conv) {
-#pragma unroll
-            for (int i = 0; i < NN; ++i) res[i] = cur[i] * usc;
-          }                                   // else: keep the linear-constraint solution
-          ok = conv;
-        }
-      }
-    }
+    __syncthreads();                              // the stage is free once its stores have read it
   }
-  __syncthreads();                          // tile rows are rewritten below
-  bool finite = true;
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < NN; ++j) {
-      // TwoSum: hi + lo == ref + res exactly
-      const float s = ref + res[j];
-      const float bb = s - ref;
-      const float err = (ref - (s - bb)) + (res[j] - bb);
-      shi[tid * NN + j] = s;
-      slo[tid * NN + j] = err;
-      finite = finite && isfinite(s);
-    }
-  }
-  __syncthreads();
-  // coalesced write-back: e0 * NN is a multiple of 4 (TILE is), and so is the lo plane offset
-  const int nact = min(TILE, K - e0);
-  const int nout = nact * NN, nv = nout >> 2;
-  float4* oh = reinterpret_cast<float4*>(out + (int64_t)e0 * NN);
-  float4* ol = reinterpret_cast<float4*>(out + plane + (int64_t)e0 * NN);
-  for (int v = tid; v < nv; v += TILE) {
-    oh[v] = reinterpret_cast<const float4*>(shi)[v];
-    ol[v] = reinterpret_cast<const float4*>(slo)[v];
-  }
-  for (int idx = 4 * nv + tid; idx < nout; idx += TILE) {
-    out[(int64_t)e0 * NN + idx] = shi[idx];
-    out[plane + (int64_t)e0 * NN + idx] = slo[idx];
-  }
-  const unsigned bits = (finite ? 0u : SL_ST_NONFINITE) | (ok ? 0u : SL_ST_PICARD_NOCONV);
+  if (tid == 0) bulk_wait_all();
   if (bits) atomicOr(status, bits);
 }
 
 template <int NN>
 void launch_n(const Mixed1DParams& p, const float* in, float* out, unsigned* st, cudaStream_t s) {
-  const int grid = (p.K + TILE - 1) / TILE;
-  k_step1d_mixed<NN><<<grid, TILE, 0, s>>>(p, in, out, st);
+  // persistent grid: resident CTAs per SM times the SM count (queried once per device and n)
+  static int cached_dev = -1, cached_grid = 0;
+  constexpr size_t smem = (size_t)2 * 2 * stage_floats<NN>() * sizeof(float);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (cached_dev != dev) {
+    cudaFuncSetAttribute(k_step1d_mixed<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step1d_mixed<NN>, TILE, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cached_grid = std::max(1, per_sm) * std::max(1, sms);
+    cached_dev = dev;
+  }
+  const int ntiles = (p.K + TILE - 1) / TILE;
+  k_step1d_mixed<NN><<<std::min(ntiles, cached_grid), TILE, smem, s>>>(p, in, out, st);
 }
 
 }  // namespace k1m

@@ -451,6 +451,8 @@ sl_status check_step(sl_ctx* c, const void* phi_in, const void* phi_out, const s
                      const sl_options* opt) {
   if (!phi_in || !phi_out || !opt) return fail(c, SL_EINVAL, "null argument");
   if (phi_in == phi_out) return fail(c, SL_EINVAL, "phi_in and phi_out must be distinct buffers");
+  if (((uintptr_t)phi_in | (uintptr_t)phi_out) & 15u)
+    return fail(c, SL_EINVAL, "state buffers must be 16-byte aligned");
   if (!valid_velocity(c, vel)) return fail(c, SL_EINVAL, "bad velocity for this mesh");
   if (opt->rk_order < 1 || opt->rk_order > 4) return fail(c, SL_EINVAL, "rk_order must be 1..4");
   if (opt->fit != SL_FIT_HARD && opt->fit != SL_FIT_SOFT) return fail(c, SL_EINVAL, "bad fit mode");
