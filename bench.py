@@ -127,6 +127,23 @@ def cpu_baseline(n, seconds=12.0, cons=7):
             "sample": f"{done} elements (x{n} nodes) of one step at the pulse centre, {el:.1f} s, numpy FP64, 1 thread"}
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (the slowest rank's time); x itself on one rank.
+    Collective: every rank of the process group calls it."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, nodes, steps, seconds):
+    """Whole-job node updates per second: every rank advances its own replica of nodes nodes."""
+    return world * nodes * steps / seconds
+
+
 def run_reference(args, rank, world):
     n = args.n
     if rank != 0:
@@ -207,11 +224,8 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     status = ctx.sync()
     nodes = prob.kx * n
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * nodes * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(total_ms, world, "cuda")
+    value = job_throughput(world, nodes, args.steps, total_ms * 1e-3)
 
     # end to end through the public API: host doubles in, one step, host doubles out, every step
     e2e_steps = min(args.steps, 50)
@@ -222,8 +236,8 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for s in range(e2e_steps):
         ctx.run_host(host_in, host_out, vel, s * dt, dt, 1, opts)
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * nodes * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_value = job_throughput(world, nodes, e2e_steps, e2e_s)
 
     # the plain FP64 per-element form on the same workload, for comparison
     fp64 = None
