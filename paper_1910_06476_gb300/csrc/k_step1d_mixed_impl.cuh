@@ -124,20 +124,37 @@ __device__ __forceinline__ bool element_step(const Mixed1DParams& P, const float
   bool ok = true;
   ref = shi[own];
   float ps[NN], pu[NN];
+  if (has_up) {                             // own and upwind node i side by side (paired adds)
+    const float2 mref = make_float2(-ref, -ref);
 #pragma unroll
-  for (int i = 0; i < NN; ++i) ps[i] = (shi[own + i] - ref) + slo[own + i];
-  if (has_up) {
-#pragma unroll
-    for (int i = 0; i < NN; ++i) pu[i] = (shi[up + i] - ref) + slo[up + i];
+    for (int i = 0; i < NN; ++i) {
+      const float2 d = __fadd2_rn(make_float2(shi[own + i], shi[up + i]), mref);
+      const float2 v = __fadd2_rn(d, make_float2(slo[own + i], slo[up + i]));
+      ps[i] = v.x;
+      pu[i] = v.y;
+    }
   } else {
+#pragma unroll
+    for (int i = 0; i < NN; ++i) ps[i] = (shi[own + i] - ref) + slo[own + i];
     const float g = (float)(P.ghost - (double)ref);   // ghost value at the inflow domain face
 #pragma unroll
     for (int i = 0; i < NN; ++i) pu[i] = g;
   }
-  // shared linear operator
+  // shared linear operator; rows 2p and 2p + 1 go through the paired FP32 FMA (each lane rounds
+  // like fmaf and sums in the same order as a row on its own)
   float pl[NN];
 #pragma unroll
-  for (int j = 0; j < NN; ++j) {
+  for (int pr = 0; pr < NN / 2; ++pr) {
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int i = 0; i < NN; ++i) acc = __ffma2_rn(P.Gp[pr][i], make_float2(ps[i], ps[i]), acc);
+#pragma unroll
+    for (int i = 0; i < NN; ++i) acc = __ffma2_rn(P.Gp[pr][NN + i], make_float2(pu[i], pu[i]), acc);
+    pl[2 * pr] = acc.x;
+    pl[2 * pr + 1] = acc.y;
+  }
+  if (NN & 1) {
+    constexpr int j = NN - 1;
     float acc = 0.0f;
 #pragma unroll
     for (int i = 0; i < NN; ++i) acc = fmaf(P.Gs[j * NN + i], ps[i], acc);
@@ -174,9 +191,10 @@ __device__ __forceinline__ bool element_step(const Mixed1DParams& P, const float
         escale = fmaf(P.w[i], phv * phv, escale);
       }
       for (int s = 0; s < P.nst; ++s) {
-        float es = 0.0f, eu = 0.0f;
+        float2 eo = make_float2(0.0f, 0.0f);    // (own, upwind) basis sums, paired
 #pragma unroll
-        for (int i = 0; i < NN; ++i) { es = fmaf(P.E[s][i], qs[i], es); eu = fmaf(P.E[s][i], qu[i], eu); }
+        for (int i = 0; i < NN; ++i) eo = __ffma2_rn(make_float2(P.E[s][i], P.E[s][i]), make_float2(qs[i], qu[i]), eo);
+        const float es = eo.x, eu = eo.y;
         gv = fmaf(P.lam * P.fb[s], es * es - eu * eu, gv);
         gm = fmaf(P.lam * P.fb[s], es - eu, gm);
       }
@@ -316,9 +334,24 @@ __global__ void __launch_bounds__(TILE, NN <= 11 ? 3 : 2)
     __syncthreads();                              // the stage's rows are rewritten below
     if (active) {
       bool finite = true;
+      // TwoSum: hi + lo == ref + res exactly; nodes j and j + 1 in paired operations
+      // (a - b is formed as fma(b, -1, a), the same single rounding)
+      const float2 rr = make_float2(ref, ref), m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-      for (int j = 0; j < NN; ++j) {
-        // TwoSum: hi + lo == ref + res exactly
+      for (int j = 0; j + 1 < NN; j += 2) {
+        const float2 r = make_float2(res[j], res[j + 1]);
+        const float2 s2 = __fadd2_rn(rr, r);
+        const float2 bb = __ffma2_rn(rr, m1, s2);                  // s - ref
+        const float2 t = __ffma2_rn(__ffma2_rn(bb, m1, s2), m1, rr);   // ref - (s - bb)
+        const float2 err = __fadd2_rn(t, __ffma2_rn(bb, m1, r));    // + (res - bb)
+        shi[tid * NN + j] = s2.x;
+        shi[tid * NN + j + 1] = s2.y;
+        slo[tid * NN + j] = err.x;
+        slo[tid * NN + j + 1] = err.y;
+        finite = finite && isfinite(s2.x) && isfinite(s2.y);
+      }
+      if (NN & 1) {
+        constexpr int j = NN - 1;
         const float s = ref + res[j];
         const float bb = s - ref;
         const float err = (ref - (s - bb)) + (res[j] - bb);

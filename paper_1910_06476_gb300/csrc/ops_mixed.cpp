@@ -137,6 +137,11 @@ bool build_mixed1d(const sl_ctx* c, const FitOps& fit, double a, double dt, unsi
   P.energy_on = (cons & SL_C_ENERGY) ? 1 : 0;
   P.nst = (int)feet.size();
   for (int j = 0; j < n * n; ++j) { P.Gs[j] = (float)Gs[j]; P.Gu[j] = (float)Gu[j]; }
+  for (int pr = 0; pr < n / 2; ++pr)
+    for (int i = 0; i < n; ++i) {
+      P.Gp[pr][i] = make_float2(P.Gs[2 * pr * n + i], P.Gs[(2 * pr + 1) * n + i]);
+      P.Gp[pr][n + i] = make_float2(P.Gu[2 * pr * n + i], P.Gu[(2 * pr + 1) * n + i]);
+    }
   for (int j = 0; j < n; ++j) P.w[j] = (float)w[j];
   for (int s = 0; s < P.nst; ++s) {
     P.fb[s] = (float)fb[s];

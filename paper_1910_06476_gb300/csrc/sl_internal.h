@@ -176,6 +176,7 @@ struct Mixed1DParams {
   float picard_rtol;
   int picard_cap;
   float Gs[NMAX * NMAX], Gu[NMAX * NMAX];  // [j][i]
+  float2 Gp[NMAX / 2][2 * NMAX];         // rows 2p and 2p + 1 side by side: [p][i] self, [p][n + i] upwind
   float w[NMAX];
   float fb[3];                           // merged RK weights of the distinct stage times
   float E[3][NMAX];                      // basis at the characteristic feet of the outflow face
