@@ -302,7 +302,7 @@ def run_ours(args, rank, world, local_rank):
             "fp64_per_element": fp64,
             "device_status": status}
     if not args.no_configs:
-        line["configs"] = secondary_configs(sl, torch, flush, full=args.all_configs)
+        line["configs"] = secondary_configs(sl, torch, flush, full=args.all_configs, only=args.only_config)
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n, seconds=args.ref_seconds)
     print(json.dumps(line), flush=True)
@@ -344,7 +344,7 @@ def measure_config(sl, torch, prob, precision, steps, flush, phi=None):
         ctx, vel, dt, opts)
 
 
-def secondary_configs(sl, torch, flush, full=False):
+def secondary_configs(sl, torch, flush, full=False, only=None):
     """The other configurations of the measurement plan on both paths, outside the headline timed
     region (the 2048^2 swirl and the 64-problem batch only with full=True)."""
     res = []
@@ -356,6 +356,8 @@ def secondary_configs(sl, torch, flush, full=False):
                  10))
     if full:
         plan.append(("2d_swirl_2048x2048_n8 (config 5)", sl_inputs.config5_swirl(), [sl.MIXED, sl.FP64], 3))
+    if only is not None:
+        plan = [p for p in plan if f"(config {only})" in p[0]]
     for name, prob, precs, steps in plan:
         entry = {"workload": name, "nodes": None}
         phi0, outs = None, {}
@@ -397,7 +399,8 @@ def secondary_configs(sl, torch, flush, full=False):
         del outs, phi0
         torch.cuda.empty_cache()
         res.append(entry)
-    res.append(measure_batch(sl, torch, flush, nprob=64 if full else 16))
+    if only is None:
+        res.append(measure_batch(sl, torch, flush, nprob=64 if full else 16))
     return res
 
 
@@ -464,6 +467,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the other configurations")
     ap.add_argument("--all-configs", action="store_true",
                     help="add the 2048^2 swirl and the 64-problem batch to the other configurations")
+    ap.add_argument("--only-config", type=int, default=None, help="of the other configurations, only this one")
     ap.add_argument("--quick-configs", action="store_true", help="(default) other configurations, smaller set")
     args = ap.parse_args()
     if args.warmup < 3:

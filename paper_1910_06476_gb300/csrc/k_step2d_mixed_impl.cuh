@@ -143,6 +143,13 @@ template <int NN>
 struct Shape {
   static constexpr int ND = NN * NN;
   static constexpr int NT = ((ND > 4 * NN ? ND : 4 * NN) + 31) / 32 * 32;
+  // resident CTAs asked of the compiler (one element per CTA keeps the SM latency-bound): register
+  // caps of 64 per thread for n <= 9 (a few bytes of spill at most), about 100 for n <= 12, 128
+  // above
+  static constexpr int MINB = NN <= 9 ? 65536 / (64 * NT) : NN <= 12 ? 65536 / (96 * NT)
+                                                           : (65536 / (128 * NT) > 1 ? 65536 / (128 * NT) : 1);
+  // phase 2 (less register demand): 64 for n <= 9, about 96 above
+  static constexpr int MINB2 = NN <= 9 ? 65536 / (64 * NT) : 65536 / (96 * NT);
 };
 
 // per-problem float parameters of a batch element (the FP64 geometry is already in P)
@@ -176,12 +183,14 @@ __device__ __forceinline__ double lref(float r0, float gx, float gy, double xi, 
 }
 
 template <int NN>
-__global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, const __grid_constant__ Mixed2DExtra X0,
+__global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB) k_p1(StepParams P0, const __grid_constant__ Mixed2DExtra X0,
                                                      Map2D M, const float* __restrict__ in, Work2M W,
                                                      unsigned* status) {
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
   __shared__ float s_xi[NN], s_lam[NN], s_w[NN], s_l0[NN], s_l1[NN];
-  __shared__ float s_psi[ND], s_ph[ND], s_t[ND], s_r[ND], s_Rx[ND], s_Ry[ND];
+  constexpr int NP = (NN + 3) & ~3;                // psihat rows padded to 16 bytes
+  __shared__ float s_psi[ND], s_t[ND], s_r[ND], s_Rx[ND], s_Ry[ND];
+  __shared__ __align__(16) float s_ph[NN * NP];
   __shared__ float s_red[NT / 32];
   __shared__ float s_face[4][NMAX][4];
   __shared__ int s_nq[4];
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, const __gri
       float acc = 0.0f;
 #pragma unroll
       for (int q = 0; q < NN; ++q) acc = fmaf(s_Ry[j * NN + q], s_t[q * NN + i], acc);
-      s_ph[tid] = first ? acc : s_ph[tid] + acc;
+      s_ph[j * NP + i] = first ? acc : s_ph[j * NP + i] + acc;
     }
     __syncthreads();
   };
@@ -261,12 +270,27 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, const __gri
   for (int it = 0; it < SOLVE_CAP; ++it) {
     float r = 0.0f;
     if (part) {
+      // row sums: every thread reads the same psihat row (16-byte broadcast loads), even and odd
+      // columns accumulate in the two lanes of paired FMAs
       float acc = 0.0f;
 #pragma unroll 1
       for (int mm = 0; mm < NN; ++mm) {
-        float row = 0.0f;
+        const float4* rowp = reinterpret_cast<const float4*>(s_ph + mm * NP);
+        float2 r2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int l = 0; l < NN; ++l) row = fmaf(s_ph[mm * NN + l], Lx[l], row);
+        for (int q = 0; q < NN / 4; ++q) {
+          const float4 v = rowp[q];
+          r2 = __ffma2_rn(make_float2(v.x, v.y), make_float2(Lx[4 * q], Lx[4 * q + 1]), r2);
+          r2 = __ffma2_rn(make_float2(v.z, v.w), make_float2(Lx[4 * q + 2], Lx[4 * q + 3]), r2);
+        }
+        float row = r2.x + r2.y;
+        if (NN % 4 != 0) {
+          const float4 v = rowp[NN / 4];
+          constexpr int l0 = NN & ~3;
+          row = fmaf(v.x, Lx[l0], row);
+          if (NN % 4 > 1) row = fmaf(v.y, Lx[(l0 + 1) % NN], row);
+          if (NN % 4 > 2) row = fmaf(v.z, Lx[(l0 + 2) % NN], row);
+        }
         acc = fmaf(Ly[mm], row, acc);
       }
       r = ps - acc;
@@ -279,7 +303,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, const __gri
     const bool diverging = !(rmax <= 4.0f * best);                             // or not finite
     if (stalled || diverging) {
       if (!(rmax <= best)) {                  // back to the best iterate
-        if (part) s_ph[tid] = s_best[tid];
+        if (part) s_ph[j * NP + i] = s_best[tid];
         __syncthreads();
       }
       solved = fminf(rmax, best) <= SOLVE_FLOOR * scale;
@@ -287,13 +311,13 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, const __gri
     }
     if (rmax < best) {
       best = rmax;
-      if (part) s_best[tid] = s_ph[tid];
+      if (part) s_best[tid] = s_ph[j * NP + i];
     }
     prev = rmax;
     precond_add(false);
   }
   if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);
-  if (part) W.psihat[E.base + tid] = s_ph[tid];
+  if (part) W.psihat[E.base + tid] = s_ph[j * NP + i];
   // element sums of psi^n (reference measure)
   const float w2 = part ? s_w[i] * s_w[j] : 0.0f;
   const float m1 = block_sum<NT>(w2 * pn, s_red);
@@ -311,7 +335,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, const __gri
     const float* L = (f == 1 || f == 3) ? s_l1 : s_l0;
     float acc = 0.0f;
 #pragma unroll
-    for (int k = 0; k < NN; ++k) acc = fmaf(f < 2 ? s_ph[q * NN + k] : s_ph[k * NN + q], L[k], acc);
+    for (int k = 0; k < NN; ++k) acc = fmaf(f < 2 ? s_ph[q * NP + k] : s_ph[k * NP + q], L[k], acc);
     W.traces[E.g * M.tstride + tid] = acc;
   }
   // face sums over the step; a face shared with a neighbour of another node count takes the rule
@@ -375,7 +399,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, const __gri
 }
 
 template <int NN>
-__global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, const __grid_constant__ Mixed2DExtra X0,
+__global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2) k_p2(StepParams P0, const __grid_constant__ Mixed2DExtra X0,
                                                      Map2D M, const float* __restrict__ in, Work2M W,
                                                      float* __restrict__ out, unsigned* status) {
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
@@ -438,29 +462,39 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, const __gri
   }
   const bool mass = (P.cons & SL_C_MASS) != 0, energy = (P.cons & SL_C_ENERGY) != 0;
   float netm = 0.0f, netd2 = 0.0f, nu = 0.0f;
-  if ((mass || energy) && tid == 0) {
-    // net outflow of mass (increments) and of the squared increments, plus the velocity balance
-    for (int f = 0; f < 4; ++f) {
+  if ((mass || energy) && tid < 32) {
+    // net outflow of mass (increments) and of the squared increments, plus the velocity balance:
+    // lanes 0-3 of the first warp take one face each, summed in face order
+    float cu = 0.0f, cm = 0.0f, cd = 0.0f;
+    if (tid < 4) {
+      const int f = tid;
       const float* F = W.faces + E.g * 16 + 4 * f;
       const int nb = nb_index(P, ex, ey, f);
-      nu += F[0] + F[1];
-      netm += F[2];
-      netd2 += F[3];
+      cu = F[0] + F[1];
       if (nb >= 0) {
         const float* G = W.faces + (E.gb + nb) * 16 + 4 * (f ^ 1);
         const float dref = W.elem[(E.gb + nb) * 8] - ref;
         // inflow part: u.n (dref + psi_nb) with the neighbour's u.n = -ours
-        netm += dref * F[1] - G[2];
-        netd2 += dref * dref * F[1] - 2.0f * dref * G[2] - G[3];
+        cm = F[2] + (dref * F[1] - G[2]);
+        cd = F[3] + (dref * dref * F[1] - 2.0f * dref * G[2] - G[3]);
       } else {
         const float g = (float)(P.ghost - (double)ref);
-        netm += g * F[1];
-        netd2 += g * g * F[1];
+        cm = F[2] + g * F[1];
+        cd = F[3] + g * g * F[1];
       }
     }
-    s_scal[0] = netm;
-    s_scal[1] = netd2;
-    s_scal[2] = nu;
+    float su = 0.0f, sm = 0.0f, sd = 0.0f;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      su += __shfl_sync(0xffffffffu, cu, f);
+      sm += __shfl_sync(0xffffffffu, cm, f);
+      sd += __shfl_sync(0xffffffffu, cd, f);
+    }
+    if (tid == 0) {
+      s_scal[0] = sm;
+      s_scal[1] = sd;
+      s_scal[2] = su;
+    }
   }
   __syncthreads();
   netm = s_scal[0];
