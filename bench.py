@@ -309,7 +309,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 # DRAM bytes per launch from one ncu capture of the same workload (None once the kernel changed)
-TRAFFIC = {"k_step1d_mixed": 75552000 + 25369088}   # n = 9, K = 2^20: read + written (lines still dirty
+TRAFFIC = {"k_step1d_mixed": 75550000 + 24440000}   # n = 9, K = 2^20: read + written (lines still dirty
                                                     # in L2 at kernel end are not counted)
 
 

@@ -134,10 +134,13 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
   float ps[NN];
   {
     float px[NN], py[NN];
+    const float2 mref = make_float2(-ref, -ref);
 #pragma unroll
-    for (int i = 0; i < NN; ++i) {
-      ps[i] = (s_hi[so + j * NN + i] - ref) + s_lo[so + j * NN + i];
-      px[i] = gx ? gval : (s_hi[sx + j * NN + i] - ref) + s_lo[sx + j * NN + i];
+    for (int i = 0; i < NN; ++i) {                // own and x-neighbour node side by side
+      const float2 d = __fadd2_rn(make_float2(s_hi[so + j * NN + i], s_hi[sx + j * NN + i]), mref);
+      const float2 v = __fadd2_rn(d, make_float2(s_lo[so + j * NN + i], s_lo[sx + j * NN + i]));
+      ps[i] = v.x;
+      px[i] = gx ? gval : v.y;
       py[i] = gy ? gval : (s_hi[sy + i * NN + j] - ref) + s_lo[sy + i * NN + j];
     }
     // x inflow residual pieces: upwind outflow trace minus own inflow trace, before the y-remap
@@ -162,9 +165,18 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
     s_v[el][j] = gy ? 0.0f : v;
     s_p[el][j] = pm;
   }
-  // x-remap of row j: t[j][l] = sum_i R_x[l][i] psi[j][i]
+  // x-remap of row j: t[j][l] = sum_i R_x[l][i] psi[j][i]; rows l, l + 1 in paired FMAs (each
+  // lane rounds like fmaf, in the same order)
 #pragma unroll
-  for (int l = 0; l < NN; ++l) {
+  for (int q = 0; q < NN / 2; ++q) {
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int i = 0; i < NN; ++i) acc = __ffma2_rn(P.Rxp[q][i], make_float2(ps[i], ps[i]), acc);
+    s_t[el * ND + j * NN + 2 * q] = acc.x;
+    s_t[el * ND + j * NN + 2 * q + 1] = acc.y;
+  }
+  if (NN & 1) {
+    constexpr int l = NN - 1;
     float acc = 0.0f;
 #pragma unroll
     for (int i = 0; i < NN; ++i) acc = fmaf(P.Rx[l * NN + i], ps[i], acc);
@@ -179,7 +191,15 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
 #pragma unroll
     for (int m = 0; m < NN; ++m) tc[m] = s_t[el * ND + m * NN + j];
 #pragma unroll
-    for (int k = 0; k < NN; ++k) {
+    for (int q = 0; q < NN / 2; ++q) {
+      float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int m = 0; m < NN; ++m) acc = __ffma2_rn(P.Ryp[q][m], make_float2(tc[m], tc[m]), acc);
+      ph[2 * q] = acc.x;
+      ph[2 * q + 1] = acc.y;
+    }
+    if (NN & 1) {
+      constexpr int k = NN - 1;
       float acc = 0.0f;
 #pragma unroll
       for (int m = 0; m < NN; ++m) acc = fmaf(P.Ry[k * NN + m], tc[m], acc);
@@ -238,8 +258,30 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
     const float l0j = __ldg(tab + P.o_l0 + j), l1j = __ldg(tab + P.o_l1 + j);
     const float wj = __ldg(tab + P.o_w + j) * sm;
     bool finite = true;
+    // nodes k and k + 1 in paired operations, each lane in the scalar order (a - b as fma(b, -1, a))
+    const float2 rr = make_float2(ref, ref), m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-    for (int k = 0; k < NN; ++k) {
+    for (int k = 0; k + 1 < NN; k += 2) {
+      float2 acc = make_float2(ph[k], ph[k + 1]);
+      acc = __ffma2_rn(make_float2(sS, sS), make_float2(P.l0[k], P.l0[k + 1]), acc);
+      acc = __ffma2_rn(make_float2(sN, sN), make_float2(P.l1[k], P.l1[k + 1]), acc);
+      acc = __ffma2_rn(make_float2(wj, wj), make_float2(P.w[k], P.w[k + 1]), acc);
+      if (P.bnd) {
+        acc = __ffma2_rn(make_float2(s_sw[el][k], s_sw[el][k + 1]), make_float2(l0j, l0j), acc);
+        acc = __ffma2_rn(make_float2(s_se[el][k], s_se[el][k + 1]), make_float2(l1j, l1j), acc);
+      }
+      const float2 s2 = __fadd2_rn(rr, acc);
+      const float2 bb = __ffma2_rn(rr, m1, s2);                         // s - ref
+      const float2 t = __ffma2_rn(__ffma2_rn(bb, m1, s2), m1, rr);      // ref - (s - bb)
+      const float2 e = __fadd2_rn(t, __ffma2_rn(bb, m1, acc));          // + (acc - bb)
+      s_hi[so + k * NN + j] = s2.x;
+      s_hi[so + (k + 1) * NN + j] = s2.y;
+      s_lo[so + k * NN + j] = e.x;
+      s_lo[so + (k + 1) * NN + j] = e.y;
+      finite = finite && isfinite(s2.x) && isfinite(s2.y);
+    }
+    if (NN & 1) {
+      constexpr int k = NN - 1;
       float acc = ph[k];
       acc = fmaf(sS, P.l0[k], acc);
       acc = fmaf(sN, P.l1[k], acc);

@@ -117,6 +117,11 @@ bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigne
       P.Rx[l * n + q] = (float)Rx[l * n + q];
       P.Ry[l * n + q] = (float)Ry[l * n + q];
     }
+  for (int q = 0; q < n / 2; ++q)
+    for (int i = 0; i < n; ++i) {
+      P.Rxp[q][i] = make_float2(P.Rx[2 * q * n + i], P.Rx[(2 * q + 1) * n + i]);
+      P.Ryp[q][i] = make_float2(P.Ry[2 * q * n + i], P.Ry[(2 * q + 1) * n + i]);
+    }
   std::vector<ld> wxr(n, 0.0L), wyr(n, 0.0L);   // R_x^T w, R_y^T w: mass of psihat is wyr^T psi wxr
   for (int p = 0; p < n; ++p) {
     ld xi_in = 0.0L;

@@ -152,6 +152,7 @@ struct Mixed2DConstParams {
   double ghost;
   int64_t plane;
   float Rx[NMAX * NMAX], Ry[NMAX * NMAX];   // remap matrices [l][p]: l_p(xi_l - shift)
+  float2 Rxp[NMAX / 2][NMAX], Ryp[NMAX / 2][NMAX];   // rows 2q and 2q + 1 side by side
   float xix[NMAX];                          // R_x^T l_in,x: own inflow x-trace functional of a row
   float rox[NMAX], roy[NMAX];               // R^T l_out: upwind neighbour outflow-trace functionals
   float liny[NMAX];                         // l_in,y: inflow y-trace of a remapped column
