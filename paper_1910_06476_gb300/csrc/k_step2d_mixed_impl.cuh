@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2) k_p2(StepPara
   float phL = ph;
   if (part) {
     float acc = ph;
-    for (int k = 0; k < m; ++k) acc = fmaf(X.Cp[(size_t)tid * m + k], s_r[k], acc);
+    for (int k = 0; k < m; ++k) acc = fmaf(X.Cp[(size_t)k * ND + tid], s_r[k], acc);
     phL = acc;
   }
   float cur = phL;
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2) k_p2(StepPara
         float q = 0.0f;
         if (part) {
           float acc = a;
-          for (int k = 0; k < m; ++k) acc = fmaf(-X.Cp[(size_t)tid * m + k], s_ca[k], acc);
+          for (int k = 0; k < m; ++k) acc = fmaf(-X.Cp[(size_t)k * ND + tid], s_ca[k], acc);
           q = acc;
         }
         float alpha = block_sum<NT>(w2 * ql * q, s_red);

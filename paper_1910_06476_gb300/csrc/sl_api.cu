@@ -139,7 +139,15 @@ void build_ntab(sl_ntab& t, int n, int basis, int dim, bool mixed2d, TableBufs& 
     t.f_off[2] = B.fput(t.b.w);
     t.f_off[3] = B.fput(t.b.l0);
     t.f_off[4] = B.fput(t.b.l1);
-    for (int mask = 0; mask < 4; ++mask) t.f_cp[mask] = B.fput(t.fit[mask][0].Cpinv);
+    // the float pseudo-inverse is stored row of C first ([k][node]), so that the threads of an
+    // element (one per node) read consecutive floats
+    for (int mask = 0; mask < 4; ++mask) {
+      const FitOps& f = t.fit[mask][0];
+      std::vector<double> tr(f.Cpinv.size());
+      for (int q = 0; q < f.nd; ++q)
+        for (int k = 0; k < f.m; ++k) tr[(size_t)k * f.nd + q] = f.Cpinv[(size_t)q * f.m + k];
+      t.f_cp[mask] = B.fput(tr);
+    }
   }
 }
 

@@ -122,7 +122,7 @@ struct Mixed2DExtra {
   const float* w;
   const float* l0;
   const float* l1;
-  const float* Cp;                       // [n^2][m] pseudo-inverse of the active rows (hard fit)
+  const float* Cp;                       // [m][n^2] pseudo-inverse of the active rows (hard fit)
   const float* rules;                    // [NMAX + 1][3][NMAX] xi, lam, w of every node count
   const double* xid;                     // the nodes again, in double (element reference values)
   int linref;                            // 1: linear element reference (no energy row), 0: constant
