@@ -144,9 +144,9 @@ struct Shape {
   static constexpr int ND = NN * NN;
   static constexpr int NT = ((ND > 4 * NN ? ND : 4 * NN) + 31) / 32 * 32;
   // resident CTAs asked of the compiler (one element per CTA keeps the SM latency-bound): register
-  // caps of 64 per thread for n <= 9 (a few bytes of spill at most), about 100 for n <= 12, 128
-  // above
-  static constexpr int MINB = NN <= 9 ? 65536 / (64 * NT) : NN <= 12 ? 65536 / (96 * NT)
+  // caps of 64 per thread for n <= 9 (a few bytes of spill at most), about 100 for n <= 13, 128
+  // above (a tighter cap spills there and runs slower)
+  static constexpr int MINB = NN <= 9 ? 65536 / (64 * NT) : NN <= 13 ? 65536 / (96 * NT)
                                                            : (65536 / (128 * NT) > 1 ? 65536 / (128 * NT) : 1);
   // phase 2 (less register demand): 64 for n <= 9, about 96 above
   static constexpr int MINB2 = NN <= 9 ? 65536 / (64 * NT) : 65536 / (96 * NT);
