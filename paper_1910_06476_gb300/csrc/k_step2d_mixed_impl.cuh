@@ -35,6 +35,36 @@ static __constant__ float c_rk_a[5][4][4] = {
 static __constant__ float c_rk_b[5][4] = {
     {}, {1.0f}, {0.5f, 0.5f}, {1.0f / 6, 2.0f / 3, 1.0f / 6}, {1.0f / 6, 1.0f / 3, 1.0f / 3, 1.0f / 6}};
 static __constant__ float c_rk_c[5][4] = {{}, {0.0f}, {0.0f, 1.0f}, {0.0f, 0.5f, 1.0f}, {0.0f, 0.5f, 0.5f, 1.0f}};
+// distinct stage times of the face-flux quadrature and their summed weights (RK4's two c = 1/2
+// stages see the same face velocity and the same foot)
+static __constant__ int c_ds_n[5] = {0, 1, 2, 3, 3};
+static __constant__ float c_ds_c[5][3] = {{}, {0.0f}, {0.0f, 1.0f}, {0.0f, 0.5f, 1.0f}, {0.0f, 0.5f, 1.0f}};
+static __constant__ float c_ds_b[5][3] = {
+    {}, {1.0f}, {0.5f, 0.5f}, {1.0f / 6, 2.0f / 3, 1.0f / 6}, {1.0f / 6, 1.0f / 3 + 1.0f / 3, 1.0f / 6}};
+
+// sum_l row[l] b[l] over a row of NN values stored 16-byte aligned: the row is read with 16-byte
+// loads (a broadcast when every thread reads the same row), even and odd columns accumulate in
+// the two lanes of paired FMAs
+template <int NN>
+__device__ __forceinline__ float row_dot(const float* row, const float (&b)[NN]) {
+  const float4* rowp = reinterpret_cast<const float4*>(row);
+  float2 r2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int q = 0; q < NN / 4; ++q) {
+    const float4 v = rowp[q];
+    r2 = __ffma2_rn(make_float2(v.x, v.y), make_float2(b[4 * q], b[4 * q + 1]), r2);
+    r2 = __ffma2_rn(make_float2(v.z, v.w), make_float2(b[4 * q + 2], b[4 * q + 3]), r2);
+  }
+  float r = r2.x + r2.y;
+  if (NN % 4 != 0) {
+    const float4 v = rowp[NN / 4];
+    constexpr int l0 = NN & ~3;
+    r = fmaf(v.x, b[l0], r);
+    if (NN % 4 > 1) r = fmaf(v.y, b[(l0 + 1) % NN], r);
+    if (NN % 4 > 2) r = fmaf(v.z, b[(l0 + 2) % NN], r);
+  }
+  return r;
+}
 
 constexpr int SOLVE_CAP = 40;
 constexpr float SOLVE_RTOL = 3e-7f;          // target, relative to max |psi*|
@@ -189,10 +219,11 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB) k_p1(StepParam
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
   __shared__ float s_xi[NN], s_lam[NN], s_w[NN], s_l0[NN], s_l1[NN];
   constexpr int NP = (NN + 3) & ~3;                // psihat rows padded to 16 bytes
-  __shared__ float s_psi[ND], s_t[ND], s_r[ND], s_Rx[ND], s_Ry[ND];
+  __shared__ float s_t[ND], s_r[ND], s_Rx[ND], s_Ry[ND];
+  __shared__ __align__(16) float s_psi[NN * NP];   // psi^n rows, padded like psihat
   __shared__ __align__(16) float s_ph[NN * NP];
   __shared__ float s_red[NT / 32];
-  __shared__ float s_face[4][NMAX][4];
+  __shared__ float s_fs[4][NMAX][3][4];          // face point x distinct stage partial sums
   __shared__ int s_nq[4];
   const int tid = threadIdx.x;
   StepParams P = P0;
@@ -217,7 +248,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB) k_p1(StepParam
     gy = ((c10 + c11) - (c00 + c01)) * span;
   }
   if (part)
-    s_psi[tid] = (float)(((double)in[E.base + tid] + (double)in[X.plane + E.base + tid]) -
+    s_psi[j * NP + i] = (float)(((double)in[E.base + tid] + (double)in[X.plane + E.base + tid]) -
                          lref(ref, gx, gy, X.xid[i], X.xid[j]));
   __syncthreads();
 
@@ -228,7 +259,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB) k_p1(StepParam
     rk_disp(P, X, x0, y0, s_xi[i], s_xi[j], ddx, ddy, X.tT, X.dt, X.dtT);
     basis_at<NN>(s_xi, s_lam, s_xi[i], ddx, Lx);
     basis_at<NN>(s_xi, s_lam, s_xi[j], ddy, Ly);
-    pn = s_psi[tid];
+    pn = s_psi[j * NP + i];
     ps = pn - fmaf(gx, ddx, gy * ddy);       // collocation data of phihat - L
     dxs = ddx;
     dys = ddy;
@@ -270,27 +301,11 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB) k_p1(StepParam
   for (int it = 0; it < SOLVE_CAP; ++it) {
     float r = 0.0f;
     if (part) {
-      // row sums: every thread reads the same psihat row (16-byte broadcast loads), even and odd
-      // columns accumulate in the two lanes of paired FMAs
+      // row sums: every thread reads the same psihat row
       float acc = 0.0f;
 #pragma unroll 1
       for (int mm = 0; mm < NN; ++mm) {
-        const float4* rowp = reinterpret_cast<const float4*>(s_ph + mm * NP);
-        float2 r2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int q = 0; q < NN / 4; ++q) {
-          const float4 v = rowp[q];
-          r2 = __ffma2_rn(make_float2(v.x, v.y), make_float2(Lx[4 * q], Lx[4 * q + 1]), r2);
-          r2 = __ffma2_rn(make_float2(v.z, v.w), make_float2(Lx[4 * q + 2], Lx[4 * q + 3]), r2);
-        }
-        float row = r2.x + r2.y;
-        if (NN % 4 != 0) {
-          const float4 v = rowp[NN / 4];
-          constexpr int l0 = NN & ~3;
-          row = fmaf(v.x, Lx[l0], row);
-          if (NN % 4 > 1) row = fmaf(v.y, Lx[(l0 + 1) % NN], row);
-          if (NN % 4 > 2) row = fmaf(v.z, Lx[(l0 + 2) % NN], row);
-        }
+        const float row = row_dot<NN>(s_ph + mm * NP, Lx);
         acc = fmaf(Ly[mm], row, acc);
       }
       r = ps - acc;
@@ -346,10 +361,13 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB) k_p1(StepParam
       s_nq[tid] = nb < 0 ? NN : max(NN, order_of<NN>(M, E.gb + nb));
     }
     __syncthreads();
-    for (int idx = tid; idx < 4 * NMAX; idx += NT) {
-      const int f = idx / NMAX, q = idx % NMAX;
+    // one work item per (face, point, distinct stage time), partial sums kept per item and added
+    // in a fixed order below
+    const int S = c_ds_n[P.rk];
+    for (int idx = tid; idx < 4 * NMAX * 3; idx += NT) {
+      const int f = idx / (NMAX * 3), q = (idx / 3) % NMAX, s = idx % 3;
       const int nq = s_nq[f];
-      if (q >= nq) continue;
+      if (q >= nq || s >= S) continue;
       const float* rule = X.rules + (size_t)nq * 3 * NMAX;
       const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : rule[q];
       const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : rule[q];
@@ -357,42 +375,35 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB) k_p1(StepParam
       const float sg = (f == 0 || f == 2) ? -1.0f : 1.0f;
       const float Wq = (f < 2 ? X.hy : X.hx) * rule[2 * NMAX + q];
       float uo = 0.0f, ui = 0.0f, p1 = 0.0f, p2 = 0.0f;
-      const int S = c_rk_s[P.rk];
-      for (int s = 0; s < S; ++s) {
-        const float cs = c_rk_c[P.rk][s];
-        float ur, vr;
-        vel_ref(P, X, fmaf(X.hx, xr, x0), fmaf(X.hy, yr, y0), fmaf(cs, X.dtT, X.tT), ur, vr);
-        const float un = sg * (f < 2 ? ur : vr) * hn;
-        const float bw = c_rk_b[P.rk][s] * Wq * un;
-        if (un > (float)TIE) {
-          uo += bw;
-          float fdx = 0.0f, fdy = 0.0f;
-          if (cs != 0.0f) rk_disp(P, X, x0, y0, xr, yr, fdx, fdy, fmaf(cs, X.dtT, X.tT), -cs * X.dt, -cs * X.dtT);
-          float bx[NN], by[NN];
-          basis_at<NN>(s_xi, s_lam, xr, fdx, bx);
-          basis_at<NN>(s_xi, s_lam, yr, fdy, by);
-          float val = 0.0f;
+      const float cs = c_ds_c[P.rk][s];
+      float ur, vr;
+      vel_ref(P, X, fmaf(X.hx, xr, x0), fmaf(X.hy, yr, y0), fmaf(cs, X.dtT, X.tT), ur, vr);
+      const float un = sg * (f < 2 ? ur : vr) * hn;
+      const float bw = c_ds_b[P.rk][s] * Wq * un;
+      if (un > (float)TIE) {
+        uo = bw;
+        float fdx = 0.0f, fdy = 0.0f;
+        if (cs != 0.0f) rk_disp(P, X, x0, y0, xr, yr, fdx, fdy, fmaf(cs, X.dtT, X.tT), -cs * X.dt, -cs * X.dtT);
+        float bx[NN], by[NN];
+        basis_at<NN>(s_xi, s_lam, xr, fdx, bx);
+        basis_at<NN>(s_xi, s_lam, yr, fdy, by);
+        float val = 0.0f;
 #pragma unroll 1
-          for (int mm = 0; mm < NN; ++mm) {
-            float row = 0.0f;
-#pragma unroll
-            for (int l = 0; l < NN; ++l) row = fmaf(s_psi[mm * NN + l], bx[l], row);
-            val = fmaf(by[mm], row, val);
-          }
-          val += fmaf(gx, (xr - 0.5f) + fdx, gy * ((yr - 0.5f) + fdy));   // phi - r0 = (L - r0) + psi
-          p1 = fmaf(bw, val, p1);
-          p2 = fmaf(bw * val, val, p2);
-        } else if (un < -(float)TIE) {
-          ui += bw;
-        }
+        for (int mm = 0; mm < NN; ++mm) val = fmaf(by[mm], row_dot<NN>(s_psi + mm * NP, bx), val);
+        val += fmaf(gx, (xr - 0.5f) + fdx, gy * ((yr - 0.5f) + fdy));   // phi - r0 = (L - r0) + psi
+        p1 = bw * val;
+        p2 = p1 * val;
+      } else if (un < -(float)TIE) {
+        ui = bw;
       }
-      s_face[f][q][0] = uo; s_face[f][q][1] = ui; s_face[f][q][2] = p1; s_face[f][q][3] = p2;
+      s_fs[f][q][s][0] = uo; s_fs[f][q][s][1] = ui; s_fs[f][q][s][2] = p1; s_fs[f][q][s][3] = p2;
     }
     __syncthreads();
     if (tid < 16) {
       const int f = tid >> 2, k = tid & 3;
       float acc = 0.0f;
-      for (int q = 0; q < s_nq[f]; ++q) acc += s_face[f][q][k];
+      for (int q = 0; q < s_nq[f]; ++q)
+        for (int s = 0; s < S; ++s) acc += s_fs[f][q][s][k];
       W.faces[E.g * 16 + tid] = acc;
     }
   }
