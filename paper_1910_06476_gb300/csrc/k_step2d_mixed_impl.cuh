@@ -155,6 +155,31 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return s;
 }
 
+// two block sums in one pass (each component summed exactly as block_sum would); red holds
+// 2 NT / 32 floats
+template <int NT>
+__device__ __forceinline__ float2 block_sum2(float a, float b, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  __syncthreads();
+  if (ln == 0) {
+    red[w] = a;
+    red[NT / 32 + w] = b;
+  }
+  __syncthreads();
+  float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) {
+    sa += red[i];
+    sb += red[NT / 32 + i];
+  }
+  return make_float2(sa, sb);
+}
+
 template <int NT>
 __device__ __forceinline__ float block_max(float v, float* red) {
 #pragma unroll
@@ -419,6 +444,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2) k_p2(StepPara
   __shared__ float s_ph[ND], s_a[ND];
   __shared__ float s_r[MMAX], s_ca[MMAX];
   __shared__ float s_red[NT / 32];
+  __shared__ float s_red2[2 * (NT / 32)];
   __shared__ float s_scal[4];
   const int tid = threadIdx.x;
   StepParams P = P0;
@@ -536,8 +562,8 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2) k_p2(StepPara
                                       lref(ref, gx, gy, X.xid[i], X.xid[j]))
                             : 0.0f;
     const float dpsi = part ? phL - psin : 0.0f;
-    const float ev = block_sum<NT>(w2 * dpsi * (phL + (phL - dpsi)), s_red);
-    const float ml = block_sum<NT>(w2 * phL, s_red);
+    const float2 evml = block_sum2<NT>(w2 * dpsi * (phL + (phL - dpsi)), w2 * phL, s_red2);
+    const float ev = evml.x, ml = evml.y;
     const float m1 = W.elem[E.g * 8 + 3];
     float gamma;
     if (mass) gamma = ev + lam * netd2;
@@ -575,9 +601,10 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2) k_p2(StepPara
           for (int k = 0; k < m; ++k) acc = fmaf(-X.Cp[(size_t)k * ND + tid], s_ca[k], acc);
           q = acc;
         }
-        float alpha = block_sum<NT>(w2 * ql * q, s_red);
+        const float2 ab = block_sum2<NT>(w2 * ql * q, w2 * q * q, s_red2);
+        float alpha = ab.x;
         if (!mass) alpha = fmaf(rf, block_sum<NT>(w2 * q, s_red), alpha);
-        const float beta = block_sum<NT>(w2 * q * q, s_red);
+        const float beta = ab.y;
         float s;
         if (beta <= 0.0f) { s = 0.0f; feasible = gm <= 0.0f; }
         else {
