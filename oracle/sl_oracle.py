@@ -55,8 +55,12 @@ in the design notes):
 Parity pins (see tests/test_oracle_*.py): nodes/weights against numpy's leggauss and
 monomial exactness; basis cardinality and polynomial reproduction; exact translation of
 polynomial data; exact 2D Kronecker collocation; constraint satisfaction to round-off;
-global mass/energy telescoping; exponential convergence in N; the paper's time step
-1.97e-2 (Sec. 5.2).  Parity unpinned: the MF/MEF error values of the paper's tables.
+global mass/energy telescoping (also across p-nonconforming faces); exponential convergence in
+N; the paper's time step 1.97e-2 (Sec. 5.2); the paper's printed errors of tab. h_conv
+(Basecase, H = 5, 6, 7) and of tab. 3 (Basecase2, MF2, MF3 to every printed digit, Basecase1
+within 1 %).  Parity unpinned: the MF1 and MEF rows of tab. 3 (the paper does not state the
+first-order flux and energy rules they use; this oracle gives -0.0089 / 0.9822 / 4.50e-2 for
+MF1 against the printed -0.0061 / 0.9878 / 3.11e-2).
 """
 from __future__ import annotations
 
