@@ -43,6 +43,25 @@ def test_1d_exact_translation_boundary(fit, n, basis):
     np.testing.assert_allclose(out, exact, atol=1e-12)
 
 
+@pytest.mark.parametrize("fit", [O.FIT_HARD, O.FIT_SOFT])
+@pytest.mark.parametrize("a", [0.8, -0.6])
+@pytest.mark.parametrize("basis", [O.GAUSS_LEGENDRE, O.CHEB_GAUSS])
+def test_1d_exact_translation_backtracking(fit, a, basis):
+    """Interface values by backtracking (eq. 4.11: phi^n of the upwind element at the backward
+    foot of the face point), constant velocity, inflow ghost = the exact solution, cubic data: the
+    foot value is the exact phi^{n+1} at the face, so one step is the exact translate.  A wrong
+    foot (sign of the displacement, or the downwind element) breaks it."""
+    n = 6
+    s = O.Setup(1, 5, 1, (0.0, 1.0, 0, 0), n, basis, (O.BC_INFLOW,) * 4,
+                lambda x, y, t: poly1(np.asarray(x) - a * t))
+    vel = O.Vel(O.VEL_CONST, (a, 0, 0, 0, 0, 0))
+    phi = O.project_1d(s, poly1)
+    dt = O.max_dt(s, vel)
+    out, _ = O.step_1d(s, phi, O.StepOpts(vel, 0.0, dt, O.C_BOUNDARY, 4, fit, bvalue=O.BV_BACKTRACK))
+    exact = O.project_1d(s, lambda x: poly1(x - a * dt))
+    np.testing.assert_allclose(out, exact, atol=1e-12)
+
+
 @pytest.mark.parametrize("cons", [O.C_BOUNDARY | O.C_MASS, O.C_MASS])
 @pytest.mark.parametrize("rk", [3, 4])
 def test_1d_exact_translation_mass(cons, rk):
