@@ -19,7 +19,9 @@
 //   ref_e (U_out + U_in)  +  sum_f (ref_nb - ref_e) U_in,f  +  sum_f (Psi_out,f - Psi'_f),
 // Psi'_f being the neighbour's outflow flux through the shared face, so float rounding scales
 // with the variation of the data instead of |phi|.  The result is written back exactly as
-// ref + psi (TwoSum).
+// L + psi (a double sum split into hi + lo).
+// The face quadrature of phase 1 is spread over the whole CTA: one work item per (face, point,
+// distinct RK stage time), partial sums added in a fixed order (deterministic).
 #include "k_map2d.cuh"
 
 namespace sl {
