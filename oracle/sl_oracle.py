@@ -36,10 +36,14 @@ in the design notes):
       direction from the previous iterate and solving the energy equation exactly along it
       (a scalar quadratic, smallest root).  The soft fit iterates the paper's system as is.
       The energy row is applied only when the linear fit misses the energy target by more
-      than 1e-9 relative: on nearly constant data the row is almost a multiple of the mass
-      row, its direction is set by a variation near rounding level, and a correction would
-      only amplify rounding noise; 1e-9 also lies above the float resolution of the energy
-      mismatch (about eps_float (psi / phi)^2) so that all precisions decide alike.  Where the iteration does not converge within its cap (or
+      than ENERGY_SKIP_RTOL = 1e-12 relative (an argument of the step, StepOpts
+      energy_skip_rtol): the paper's iteration (Sec. 4.3, eq. remap_energy) starts from the
+      linear fit and stops when successive iterates agree, so a linear fit that already meets
+      the target to the FP64 rounding level of the energy sum (about 1e-13 for the sums of a
+      few hundred squares taken here) is its own fixed point; on nearly constant data the row
+      is then almost a multiple of the mass row, its direction is set by a variation at that
+      rounding level, and a correction would only amplify rounding noise.  1e-12 sits one
+      decade above that level.  Where the iteration does not converge within its cap (or
       ends on an unreachable target), the element keeps the linear-constraint solution and
       reports it: the paper finds the energy-constrained cases unstable, and a non-converged
       iterate has no unique value.
@@ -81,7 +85,7 @@ TIE = 1e-13                 # |u.n| at or below this is a tie (R8)
 RANK_RTOL = 1e-12           # rank decision of the pivoted QR (R6)
 PICARD_RTOL = 1e-13         # default energy-iteration tolerance, relative to max|phihat| (R7)
 PICARD_CAP = 60
-ENERGY_SKIP_RTOL = 1e-9     # energy row applied only when the linear fit misses it by more (R7)
+ENERGY_SKIP_RTOL = 1e-12    # energy row applied only when the linear fit misses it by more (R7)
 
 # ============================================================================ L0 tables
 
@@ -276,6 +280,11 @@ class StepOpts:
     bvalue: int = BV_INTERP
     picard_tol: float = None     # absolute; None -> PICARD_RTOL * max|phihat|
     picard_cap: int = PICARD_CAP
+    energy_skip_rtol: float = None   # None -> ENERGY_SKIP_RTOL (R7)
+
+
+def _skip_rtol(o):
+    return ENERGY_SKIP_RTOL if o.energy_skip_rtol is None else o.energy_skip_rtol
 
 
 def _ghost(setup, x, y, t):
@@ -335,6 +344,9 @@ def fit_soft(phihat, C, d):
     return sol
 
 
+_LAST_MISS = [0.0]      # relative energy miss of the linear fit in the last constrained_fit (reported in info)
+
+
 def energy_step_scalar(alpha, beta, gamma):
     """Smallest root s of beta s^2 + 2 alpha s + gamma = 0 (energy of phi_L + s q equals the
     target); without a real root, the s of least energy.  Returns (s, feasible)."""
@@ -350,11 +362,14 @@ def energy_step_scalar(alpha, beta, gamma):
     return -gamma / den, True
 
 
-def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode, tol, cap):
+def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode, tol, cap,
+                    skip_rtol=ENERGY_SKIP_RTOL):
     """Least-squares remap with linear constraints and optional energy (Sec. 4.3, matrix_a).
 
     ``energy_row_weights`` (w o w, flattened) switches the energy constraint on; its row
-    is (weights o phi^(k-1)), iterated over k until max|phi^(k) - phi^(k-1)| < tol.
+    is (weights o phi^(k-1)), iterated over k until max|phi^(k) - phi^(k-1)| < tol; it is
+    applied only when the linear fit misses the energy target by more than ``skip_rtol``
+    relative (R7).
     Hard fit (reading R7): the correction direction of that row, q = P a^(k) with P the
     projector onto the null space of the linear rows, is taken from the previous iterate and
     the energy equation is solved exactly along it.  Soft fit: the paper's stacked system
@@ -367,7 +382,8 @@ def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode
         W = energy_row_weights
         EL = float(np.dot(W, phiL * phiL))
         gamma = EL - E_target
-        if abs(gamma) <= ENERGY_SKIP_RTOL * max(abs(E_target), EL):
+        _LAST_MISS[0] = abs(gamma) / max(abs(E_target), EL, 1e-300)
+        if abs(gamma) <= skip_rtol * max(abs(E_target), EL):
             return phiL, 0, True
         phi = phiL
         feasible = True
@@ -387,7 +403,8 @@ def constrained_fit(phihat, C_lin, d_lin, energy_row_weights, E_target, fit_mode
     if energy_row_weights is None:
         return phi, 0, True
     EL = float(np.dot(energy_row_weights, phi * phi))
-    if abs(EL - E_target) <= ENERGY_SKIP_RTOL * max(abs(E_target), EL):
+    _LAST_MISS[0] = abs(EL - E_target) / max(abs(E_target), EL, 1e-300)
+    if abs(EL - E_target) <= skip_rtol * max(abs(E_target), EL):
         return phi, 0, True
     phiL = phi
     for it in range(1, cap + 1):
@@ -441,6 +458,18 @@ def traces_1d(setup, k, phi_k, o):
     return (lagrange(xi, (fx - xk) / setup.hx) @ phi_k) / fac
 
 
+def upwind_value(un, own, other, interior):
+    """The unique interface value at a face point (eq. 4.12a, reading R8): the trace of the
+    element the flow leaves (own when u.n_out > TIE, the neighbour's or the inflow ghost's when
+    u.n_out < -TIE); on a tie the average of both traces on an interior face, the element's own
+    trace on a non-periodic domain face.  Both elements sharing a face reach the same value."""
+    if un > TIE:
+        return own
+    if un < -TIE:
+        return other
+    return 0.5 * (own + other) if interior else own
+
+
 def _nb_1d(setup, k, side):
     """Neighbour index across the left (side=0) or right (side=1) face; None at a
     non-periodic domain boundary."""
@@ -464,15 +493,9 @@ def _face_value_1d(setup, phi, k, side, o):
     j = _nb_1d(setup, k, side)
     if j is None:
         other = float(_ghost(setup, np.array([xf]), np.array([0.0]), o.t + o.dt)[0])
-        if abs(un) <= TIE:
-            return own
     else:
         other = traces_1d(setup, j, phi[j], o)[1 - side]
-    if un > TIE:
-        return own
-    if un < -TIE:
-        return other
-    return 0.5 * (own + other)
+    return upwind_value(un, own, other, j is not None)
 
 
 def _poly_at_1d(setup, phi, e, xq):
@@ -539,9 +562,10 @@ def element_step_1d(setup, phi, k, o):
         F = _face_flux_1d(setup, phi, k, 0, o, 2) + _face_flux_1d(setup, phi, k, 1, o, 2)
         ew, Et = w, (En - o.dt * F) / h
     tol = o.picard_tol if o.picard_tol is not None else PICARD_RTOL * max(np.max(np.abs(phihat)), 1e-300)
-    new, iters, conv = constrained_fit(phihat, C, d, ew, Et, o.fit, tol, o.picard_cap)
+    _LAST_MISS[0] = 0.0
+    new, iters, conv = constrained_fit(phihat, C, d, ew, Et, o.fit, tol, o.picard_cap, _skip_rtol(o))
     return new, {"phihat": phihat, "C": C, "d": d, "iters": iters, "converged": conv,
-                 "E_target": Et}
+                 "E_target": Et, "energy_miss": _LAST_MISS[0]}
 
 
 def step_1d(setup, phi, o, elements=None):
@@ -684,14 +708,8 @@ def element_step_2d(setup, phi, ex, ey, o, phihat_cache=None):
                     Lt = L1 if face == 3 else L0
                     row = np.zeros((n, n))
                     row[:, q] = Lt                     # phi[j, i=q] * l_j(face)
-                if un[q] > TIE:
-                    val = own[q]
-                elif un[q] < -TIE:
-                    val = other[q]
-                else:
-                    val = own[q] if nb is None else 0.5 * (own[q] + other[q])
                 rows.append(row.ravel())
-                rhs.append(val)
+                rhs.append(upwind_value(un[q], own[q], other[q], nb is not None))
     W2 = hx * hy * np.outer(w, w)                          # h^d w o w, [j, i]
     phin = _get(phi, ex, ey).astype(np.float64)
     need_flux = o.constraints & (C_MASS | C_ENERGY)
@@ -732,9 +750,10 @@ def element_step_2d(setup, phi, ex, ey, o, phihat_cache=None):
     if o.constraints & C_ENERGY:
         ew, Et = w2.ravel(), (np.sum(W2 * phin ** 2) - o.dt * Fe) / (hx * hy)
     tol = o.picard_tol if o.picard_tol is not None else PICARD_RTOL * max(np.max(np.abs(ph)), 1e-300)
-    new, iters, conv = constrained_fit(ph.ravel(), C, d, ew, Et, o.fit, tol, o.picard_cap)
+    _LAST_MISS[0] = 0.0
+    new, iters, conv = constrained_fit(ph.ravel(), C, d, ew, Et, o.fit, tol, o.picard_cap, _skip_rtol(o))
     return new.reshape(n, n), {"phihat": ph, "C": C, "d": d, "iters": iters, "converged": conv,
-                               "E_target": Et}
+                               "E_target": Et, "energy_miss": _LAST_MISS[0]}
 
 
 def step_2d(setup, phi, o, elements=None):

@@ -35,7 +35,7 @@ def _stale():
     if not os.path.exists(OUT):
         return True
     t = os.path.getmtime(OUT)
-    deps = sources() + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".h")]
+    deps = sources() + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "sl.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 

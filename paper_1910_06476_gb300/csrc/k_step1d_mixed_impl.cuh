@@ -199,7 +199,7 @@ __device__ __forceinline__ bool element_step(const Mixed1DParams& P, const float
         gm = fmaf(P.lam * P.fb[s], es - eu, gm);
       }
       const float gamma = P.mass_on ? gv : fmaf(2.0f * rf, gm, gv);
-      if (fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {
+      if (fabsf(gamma) > (float)ENERGY_SKIP_RTOL_MIXED * escale) {
         float pmax = 0.0f;
 #pragma unroll
         for (int i = 0; i < NN; ++i) pmax = fmaxf(pmax, fabsf(ql[i]));

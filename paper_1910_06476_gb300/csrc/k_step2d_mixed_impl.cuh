@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2) k_p2(StepPara
     else gamma = fmaf(2.0f * ref, (ml - m1) + lam * netm, ev + lam * netd2);
     const float escale = block_sum<NT>(part ? w2 * (ref + cur) * (ref + cur) : 0.0f, s_red);
     float smax = block_max<NT>(part ? fmaxf(fabsf(phL), fabsf(ref)) : 0.0f, s_red);
-    if (smax >= 1e-30f && fabsf(gamma) > (float)ENERGY_SKIP_RTOL * escale) {
+    if (smax >= 1e-30f && fabsf(gamma) > (float)ENERGY_SKIP_RTOL_MIXED * escale) {
       int exn;
       frexpf(smax, &exn);
       const float sc = ldexpf(1.0f, -exn), usc = ldexpf(1.0f, exn);

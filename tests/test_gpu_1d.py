@@ -182,8 +182,8 @@ def test_periodic_mass_conserved_many_steps(sl):
         a, b = b, a
     assert ctx.sync() == 0
     assert abs(ctx.mass(a) - m0) < 1e-13 * abs(m0)
-    # the energy row is skipped when the linear fit already meets it to 1e-9 (per element)
-    assert abs(ctx.energy(a) - e0) < 200 * 1e-9 * abs(e0)
+    # the energy row is skipped when the linear fit already meets it to 1e-12 (per element)
+    assert abs(ctx.energy(a) - e0) < 200 * 1e-12 * abs(e0)
 
 
 def test_status_bits_and_errors(sl):
@@ -222,3 +222,24 @@ def test_run_host_matches_device_steps(sl):
         ctx.step(a, b, gv, s * dt, dt, opts)
         a, b = b, a
     assert torch.equal(a.cpu().ravel(), host_out)
+
+
+def test_energy_row_in_skip_band_fp64(sl):
+    """Gaussian pulse, K = 256, n = 9, boundary + mass + energy: about 150 elements miss the energy
+    target by a relative 1e-12 .. 1e-9 after the linear fit.  The oracle applies the energy row
+    there (reading R7, threshold 1e-12), and so must the FP64 kernel: parity at 1e-12 holds on
+    every element, including those of the band."""
+    K, n = 256, 9
+    ctx, setup = make(sl, K, n)
+    gv = sl.velocity(sl.VEL_CONST, 1.0)
+    dt = ctx.max_dt(gv, sl.RULE_PAPER)
+    x, _ = ctx.node_coords()
+    phi = np.exp(-((x - 0.5) / 0.05) ** 2)
+    got, bits = gpu_step(sl, ctx, phi, gv, 0.0, dt, sl.options(7, 4))
+    ref, infos = O.step_1d(setup, phi, O.StepOpts(O.Vel(O.VEL_CONST, (1.0, 0.0)), 0.0, dt, 7, 4))
+    miss = np.array([infos[k]["energy_miss"] for k in range(K)])
+    band = np.where((miss > 1e-12) & (miss <= 1e-9))[0]
+    assert band.size > 100, band.size
+    assert all(infos[k]["converged"] for k in range(K)) and bits == 0
+    compare(setup, got, ref)
+    compare(setup, got[band], ref[band])

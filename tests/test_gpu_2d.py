@@ -80,6 +80,11 @@ CASES = [
     (2, 2, 16, 1, (2 * np.pi, 0.5, 0.5), 1, 3, 4, 0, 0),
     (2, 2, 17, 0, (0.6, 0.9), 0, 3, 4, 0, 0),
     (3, 2, 2, 0, (0.6, 0.9), 0, 3, 4, 0, 0),
+    # axis-aligned constant velocity: every face of one direction is an upwind tie (eq. 4.12a,
+    # reading R8: interior ties average both traces, inflow domain faces keep their own)
+    (5, 4, 6, 0, (1.0, 0.0), 0, 3, 4, 0, 0),
+    (4, 5, 7, 0, (0.0, -0.7), 1, 3, 4, 0, 0),
+    (4, 4, 5, 0, (0.0, -0.7), 0, 7, 4, 0, 0),
 ]
 
 
