@@ -102,9 +102,13 @@ enum { SL_RULE_HALF_MIN_SPACING = 0, SL_RULE_PAPER = 1 };
 enum {
   SL_ST_NONFINITE = 1u,      /* a non-finite value was written                          */
   SL_ST_PICARD_NOCONV = 2u,  /* the energy iteration hit its cap or was infeasible      */
-  SL_ST_SOLVE_NOCONV = 4u,   /* the 2D collocation iteration hit its cap                */
-  SL_ST_TIMEOUT = 8u         /* a bounded wait for an asynchronous copy gave up (the step
+  SL_ST_SOLVE_NOCONV = 4u,   /* the 2D collocation iteration did not reach its tolerance
+                                (nor an accepted floor): the element keeps its best iterate */
+  SL_ST_TIMEOUT = 8u,        /* a bounded wait for an asynchronous copy gave up (the step
                                 left its output incomplete)                             */
+  SL_ST_SOLVE_FLOOR = 16u    /* SL_MIXED 2D: a collocation solve that stalled or diverged
+                                was accepted at a residual between the float floor (4e-6)
+                                and 1e-4, relative to the largest collocation datum      */
 };
 
 typedef struct {
@@ -249,6 +253,33 @@ sl_status sl_nodes_weights(const sl_ctx* ctx, int n, double* xi, double* w);
 #define SL_NOALLOC_MAX_VALUES ((int64_t)1 << 28)
 sl_status sl_integral_noalloc(const double* phi, int64_t nelem, int nper, int dim, const double* w_host,
                               int power, double scale, double* total, void* cuda_stream);
+
+/* Work counters of the two-dimensional SL_MIXED step for non-constant velocities, p-adaptive meshes
+ * and batches (the kernels that solve the collocation system of eq. 5.4 per element), summed on the
+ * device over every step since the last call:
+ *   SL_CNT_ELEMS           element updates;
+ *   SL_CNT_SOLVE_ITERS     residual evaluations of the collocation iteration (per element: the
+ *                          iterations taken, including the one that met the tolerance);
+ *   SL_CNT_SOLVE_FLOOR     solves accepted above the float floor (SL_ST_SOLVE_FLOOR);
+ *   SL_CNT_SOLVE_NOCONV    solves not accepted (SL_ST_SOLVE_NOCONV);
+ *   SL_CNT_ENERGY_APPLIED  elements whose linear fit missed the energy target, so that the energy
+ *                          iteration of Sec. 4.3 ran;
+ *   SL_CNT_PICARD_ITERS    iterations of that energy iteration;
+ *   SL_CNT_PICARD_NOCONV   elements where it did not converge and the linear-constraint fit was
+ *                          kept (SL_ST_PICARD_NOCONV).
+ * counts (host) receives SL_NCOUNTERS values; the call synchronises the context's stream and resets
+ * the counters.  Other paths leave them unchanged. */
+enum {
+  SL_CNT_ELEMS = 0,
+  SL_CNT_SOLVE_ITERS = 1,
+  SL_CNT_SOLVE_FLOOR = 2,
+  SL_CNT_SOLVE_NOCONV = 3,
+  SL_CNT_ENERGY_APPLIED = 4,
+  SL_CNT_PICARD_ITERS = 5,
+  SL_CNT_PICARD_NOCONV = 6,
+  SL_NCOUNTERS = 8
+};
+sl_status sl_counters(sl_ctx* ctx, uint64_t* counts);
 
 /* Last error message of the context (or of the last failed sl_init when ctx is null). */
 const char* sl_last_error(const sl_ctx* ctx);

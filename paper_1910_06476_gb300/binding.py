@@ -22,11 +22,14 @@ C_BOUNDARY, C_MASS, C_ENERGY = 1, 2, 4
 FIT_HARD, FIT_SOFT = 0, 1
 BV_INTERP, BV_BACKTRACK = 0, 1
 RULE_HALF_MIN_SPACING, RULE_PAPER = 0, 1
-ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV, ST_TIMEOUT = 1, 2, 4, 8
+ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV, ST_TIMEOUT, ST_SOLVE_FLOOR = 1, 2, 4, 8, 16
+COUNTERS = ("elems", "solve_iters", "solve_floor", "solve_noconv", "energy_applied", "picard_iters",
+            "picard_noconv", "reserved")
 
 EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
            "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",
-           "sl_integral_noalloc", "sl_batch_create", "sl_batch_step", "sl_batch_offset", "sl_last_error"]
+           "sl_integral_noalloc", "sl_batch_create", "sl_batch_step", "sl_batch_offset", "sl_counters",
+           "sl_last_error"]
 
 
 class SlMesh(C.Structure):
@@ -71,6 +74,7 @@ def load_library(path=LIB_PATH):
     lib.sl_mass.argtypes = [P, P, C.POINTER(C.c_double)]
     lib.sl_energy.argtypes = [P, P, C.POINTER(C.c_double)]
     lib.sl_sync.argtypes = [P, C.POINTER(C.c_uint32)]
+    lib.sl_counters.argtypes = [P, C.POINTER(C.c_uint64)]
     lib.sl_max_dt.argtypes = [P, C.POINTER(SlVelocity), C.c_int, C.POINTER(C.c_double)]
     lib.sl_state_size.argtypes = [P]
     lib.sl_state_size.restype = C.c_int64
@@ -235,6 +239,12 @@ class Context:
         if st not in (SL_OK, SL_EDEVICE):
             self._check(st)
         return bits.value
+
+    def counters(self):
+        """Work counters of the 2D mixed general kernels since the last call (sl_counters), by name."""
+        arr = (C.c_uint64 * len(COUNTERS))()
+        self._check(self._lib.sl_counters(self._h, arr))
+        return dict(zip(COUNTERS, (int(v) for v in arr)))
 
     def max_dt(self, vel, rule=RULE_HALF_MIN_SPACING):
         out = C.c_double()

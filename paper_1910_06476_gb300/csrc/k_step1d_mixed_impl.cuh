@@ -382,19 +382,9 @@ __global__ void __launch_bounds__(TILE, NN <= 11 ? 3 : 2)
 
 template <int NN>
 void launch_n(const Mixed1DParams& p, const float* in, float* out, unsigned* st, cudaStream_t s) {
-  // persistent grid: resident CTAs per SM times the SM count (queried once per device and n)
-  static int cached_dev = -1, cached_grid = 0;
+  // persistent grid: resident CTAs per SM times the SM count (cached per device and kernel)
   constexpr size_t smem = (size_t)2 * 2 * stage_floats<NN>() * sizeof(float);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (cached_dev != dev) {
-    cudaFuncSetAttribute(k_step1d_mixed<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step1d_mixed<NN>, TILE, smem);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cached_grid = std::max(1, per_sm) * std::max(1, sms);
-    cached_dev = dev;
-  }
+  const int cached_grid = persistent_grid((const void*)k_step1d_mixed<NN>, TILE, smem);
   const int ntiles = (p.K + TILE - 1) / TILE;
   k_step1d_mixed<NN><<<std::min(ntiles, cached_grid), TILE, smem, s>>>(p, in, out, st);
 }

@@ -1,27 +1,43 @@
 #pragma once
-// 2D DSEM-SL step in mixed precision for any prescribed velocity: double-float state, float
-// arithmetic on increments relative to a per-element reference value (Sec. 4, two-dimensional
-// scheme).  Same two phases as the FP64 kernels (k_step2d_impl.cuh):
-//   phase 1: advect the particles in element-local coordinates (float), solve the collocation
-//            system of eq. 5.4 for the increments psi = phi - ref by preconditioned iterative
-//            refinement, take the face traces, and integrate per face over the step
-//              U_out, U_in : RK/Gauss quadrature of u.n_out split by its sign,
-//              Psi, Psi2   : the same of u.n psi and u.n psi^2 at the feet of the outflow points;
-//   phase 2: interface values, mass and energy targets, constrained fit, energy iteration.
-// Without the energy row the element reference is linear, L = r0 + gx (xi - 1/2) + gy (eta - 1/2)
-// (from the corner values; evaluated in double wherever a node value is formed), and psi = phi - L
-// is what the float arithmetic carries: for resolved data it is smaller than phi - r0 by about the
-// element width over the data's length scale, and so is every rounding error of the remap, the
-// traces and the fit.  Particles keep phi (divergence-free velocity), so the collocation data for
-// psihat = phihat - L is psi_p - grad L . d_p (d_p the particle's displacement).  With the energy
-// row the reference is the constant r0 (gx = gy = 0).
-// Everything a target needs is assembled from increments: the net mass flux of element e is
-//   ref_e (U_out + U_in)  +  sum_f (ref_nb - ref_e) U_in,f  +  sum_f (Psi_out,f - Psi'_f),
-// Psi'_f being the neighbour's outflow flux through the shared face, so float rounding scales
-// with the variation of the data instead of |phi|.  The result is written back exactly as
-// L + psi (a double sum split into hi + lo).
-// The face quadrature of phase 1 is spread over the whole CTA: one work item per (face, point,
-// distinct RK stage time), partial sums added in a fixed order (deterministic).
+// 2D DSEM-SL step in mixed precision for any prescribed velocity (Sec. 4, two-dimensional scheme):
+// particles seeded at the Gauss nodes and advected (eq. 4.4a), the collocation system eq. 5.4 solved for
+// the remapped values, face traces (eq. 2dx/2dy_bnd_interpolate), upwinded interface values (eq. 4.12a),
+// mass and energy targets (eq. 4.14, remap_mass, remap_energy) and the constrained fit (eq. matrix_a).
+//
+// State: double-float (hi + lo floats).  The bulk arithmetic is float on increments psi = phi - L
+// relative to an element reference L, written back exactly, so float rounding scales with the
+// variation inside the element:
+//   - without the energy row L = r0 + gx (xi - 1/2) + gy (eta - 1/2) from the corner values, with the
+//     energy row the constant r0.  L at a point is an exact float-float value (two-sum of r0 and the
+//     once-rounded linear part), psi = (hi - L_hi) + (lo - L_lo) is therefore accurate relative to psi,
+//     and the write-back L + psi is a float-float sum.  No FP64 instruction is used: this GPU's FP64
+//     pipe runs at about 1/64 of the FP32 rate.
+//   - Particles keep phi (divergence-free velocity), so the collocation data of psihat = phihat - L at a
+//     particle displaced by d are psi - grad L . d.
+//   - Mass: the element mass M^n = sum w (x) w (hi + lo) and each face's outflow flux G_f (outflow points
+//     of the element, RK/Gauss quadrature at the backward characteristic feet, plus the ghost inflow on a
+//     domain face) are float-float values.  An element's net outflow is its own G_f minus its
+//     neighbours' G through the shared faces: every face flux enters two elements with opposite signs
+//     as the same number, so global mass telescopes.  The fit itself works on float increments; one
+//     refinement step then measures the element mass of the result in float-float and moves the
+//     remaining miss along the pseudo-inverse column of the mass row into the lo word, which brings the
+//     element mass to its target to about 1e-16 relative.
+//   - Energy: target and mismatch from float increments (the energy row is decided at a 1e-9 relative
+//     miss, its float resolution).
+//
+// Work layout: a group of G warps advances one element at a time (G = 1 up to n = 8, 5 at n = 17), two
+// particles per thread (p0 = t, p1 = t + 32 G) with paired float operations across them where they
+// share operands, several groups per CTA, each synchronising on its own named barrier (one warp:
+// __syncwarp).  Reductions are butterflies (every lane gets the same bits) and, across the warps of a
+// group, a fixed-order sum.  The kernels are persistent: group k of the grid walks the launch's elements
+// k, k + groups, ...; per-group counters (solve and energy iterations, elements that stopped at the
+// float floor or did not converge) are added to the context's counters once per group.
+// Swirl velocity without transcendentals in the RK stages: sin and cos of pi x at the element's node
+// and corner coordinates are taken once per element; at a displaced point they follow from the angle
+// addition formulas, with the sine and cosine of the small angle pi h d from their Taylor series (used
+// while h <= 1/4, so that |pi h d| <= pi / 4 where ten terms are exact to 1e-9; coarser meshes evaluate
+// sinpi and cospi directly).  cos(pi t / T) is taken once per element at the stage-time fractions 0,
+// 1/4, 1/2, 3/4, 1 of the step, which cover the RK schemes and their backward feet.
 #include "k_map2d.cuh"
 
 namespace sl {
@@ -44,63 +60,208 @@ static __constant__ float c_ds_c[5][3] = {{}, {0.0f}, {0.0f, 1.0f}, {0.0f, 0.5f,
 static __constant__ float c_ds_b[5][3] = {
     {}, {1.0f}, {0.5f, 0.5f}, {1.0f / 6, 2.0f / 3, 1.0f / 6}, {1.0f / 6, 1.0f / 3 + 1.0f / 3, 1.0f / 6}};
 
-// sum_l row[l] b[l] over a row of NN values stored 16-byte aligned: the row is read with 16-byte
-// loads (a broadcast when every thread reads the same row), even and odd columns accumulate in
-// the two lanes of paired FMAs
-template <int NN>
-__device__ __forceinline__ float row_dot(const float* row, const float (&b)[NN]) {
-  const float4* rowp = reinterpret_cast<const float4*>(row);
-  float2 r2 = make_float2(0.0f, 0.0f);
-#pragma unroll
-  for (int q = 0; q < NN / 4; ++q) {
-    const float4 v = rowp[q];
-    r2 = __ffma2_rn(make_float2(v.x, v.y), make_float2(b[4 * q], b[4 * q + 1]), r2);
-    r2 = __ffma2_rn(make_float2(v.z, v.w), make_float2(b[4 * q + 2], b[4 * q + 3]), r2);
-  }
-  float r = r2.x + r2.y;
-  if (NN % 4 != 0) {
-    const float4 v = rowp[NN / 4];
-    constexpr int l0 = NN & ~3;
-    r = fmaf(v.x, b[l0], r);
-    if (NN % 4 > 1) r = fmaf(v.y, b[(l0 + 1) % NN], r);
-    if (NN % 4 > 2) r = fmaf(v.z, b[(l0 + 2) % NN], r);
-  }
-  return r;
-}
-
 constexpr int SOLVE_CAP = 40;
 constexpr float SOLVE_RTOL = 3e-7f;          // target, relative to max |psi*|
 constexpr float SOLVE_STALL = 4e-6f;         // a residual that stops improving below this is the float floor
-constexpr float SOLVE_FLOOR = 1e-4f;         // best residual accepted when the iteration stalls or diverges
+constexpr float SOLVE_FLOOR = 1e-4f;         // best residual accepted (SL_ST_SOLVE_FLOOR) above the floor
 
-// velocity divided by the element size: the time derivative of the reference coordinates
-__device__ __forceinline__ void vel_ref(const StepParams& P, const Mixed2DExtra& X, float x, float y, float tT,
-                                        float& u, float& v) {
-  switch (P.vel_kind) {
-    case SL_VEL_ROTATION:
-      u = -X.om * (y - X.cy) * X.ihx;
-      v = X.om * (x - X.cx) * X.ihy;
+// ------------------------------------------------------------------ float-float arithmetic
+// Error-free transformations: Knuth's two-sum and the FMA product error.  A float-float value is the
+// unevaluated sum hi + lo with |lo| <= ulp(hi) / 2.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {   // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+// sum of two float-float values; symmetric in its arguments bit for bit (the two-sum error term is
+// exact whatever the order), so a butterfly leaves the same value in every lane
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+// product with a float-float weight, to about 2^-44 relative
+__device__ __forceinline__ ff ff_mul(ff a, ff w) {
+  const ff p = two_prod(a.hi, w.hi);
+  return fast_two_sum(p.hi, fmaf(a.hi, w.lo, fmaf(a.lo, w.hi, p.lo)));
+}
+__device__ __forceinline__ float ff_to_f(ff a) { return __fadd_rn(a.hi, a.lo); }
+
+// element reference L at reference coordinates given as (a, b) = (xi - 1/2, eta - 1/2): the linear
+// part is rounded once, L = r0 + t exactly as a float-float value.  Every use runs this same
+// instruction sequence, so both kernels agree on L bit for bit.
+__device__ __forceinline__ ff lref(float r0, float gx, float gy, float a, float b) {
+  const float t = fmaf(gx, a, __fmul_rn(gy, b));
+  return two_sum(r0, t);
+}
+
+// ------------------------------------------------------------------ groups of warps
+template <int NN>
+struct Shape {
+  static constexpr int ND = NN * NN;
+  static constexpr int G = (ND + 63) / 64;                 // warps per element
+  static constexpr int GT = 32 * G;                        // threads per element
+  static constexpr int EPC = G == 1 ? 8 : G == 2 ? 4 : G <= 4 ? 2 : 1;   // element groups per CTA
+  static constexpr int NT = GT * EPC;
+  static constexpr int NP = (NN + 3) & ~3;                 // row stride of psihat and psi^n (16 bytes)
+  static constexpr int RS = NN | 1;                        // odd row stride of the preconditioner rows
+  static constexpr int MINB = NN <= 12 ? 2 : 1;            // resident CTAs asked of the compiler
+};
+
+template <int G>
+struct Grp {
+  int t, lane, w, slot;
+  float* red;                                              // 4 G floats: two buffers of a pair per warp
+  int rb;
+  __device__ __forceinline__ void sync() const {
+    if (G == 1) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(32 * G) : "memory");
+  }
+  // Cross-warp sums alternate between two scratch buffers: a buffer is rewritten two reductions
+  // later, after every warp has passed the barrier of the reduction in between.
+  __device__ __forceinline__ float sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (G == 1) return v;
+    float* r = red + rb * 2 * G;
+    rb ^= 1;
+    if (lane == 0) r[w] = v;
+    sync();
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < G; ++k) s += r[k];
+    return s;
+  }
+  __device__ __forceinline__ float2 sum2(float a, float b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (G == 1) return make_float2(a, b);
+    float* r = red + rb * 2 * G;
+    rb ^= 1;
+    if (lane == 0) { r[w] = a; r[G + w] = b; }
+    sync();
+    float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < G; ++k) { sa += r[k]; sb += r[G + k]; }
+    return make_float2(sa, sb);
+  }
+  __device__ __forceinline__ float max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (G == 1) return v;
+    float* r = red + rb * 2 * G;
+    rb ^= 1;
+    if (lane == 0) r[w] = v;
+    sync();
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < G; ++k) s = fmaxf(s, r[k]);
+    return s;
+  }
+  __device__ __forceinline__ ff ffsum(ff v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ff u;
+      u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+      u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+      v = ff_add(v, u);
+    }
+    if (G == 1) return v;
+    float* r = red + rb * 2 * G;
+    rb ^= 1;
+    if (lane == 0) { r[w] = v.hi; r[G + w] = v.lo; }
+    sync();
+    ff s = {r[0], r[G]};
+#pragma unroll
+    for (int k = 1; k < G; ++k) s = ff_add(s, ff{r[k], r[G + k]});
+    return s;
+  }
+};
+
+// ------------------------------------------------------------------ velocity
+// sine and cosine of a small angle by their Taylor series (five terms each: exact to 1e-9 for
+// |x| <= pi / 4)
+__device__ __forceinline__ void small_sincos(float x, float& s, float& c) {
+  const float x2 = x * x;
+  float ps = fmaf(x2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(x2, ps, 1.0f / 120.0f);
+  ps = fmaf(x2, ps, -1.0f / 6.0f);
+  s = fmaf(x * x2, ps, x);
+  float pc = fmaf(x2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+  pc = fmaf(x2, pc, -1.0f / 720.0f);
+  pc = fmaf(x2, pc, 1.0f / 24.0f);
+  pc = fmaf(x2, pc, -0.5f);
+  c = fmaf(x2, pc, 1.0f);
+}
+
+// The velocity of one element divided by its size (the time derivative of the reference
+// coordinates).  A point is given by its base reference coordinates (bx, by), the sine and cosine of
+// pi times the base's physical coordinates (swirl), and a displacement (dx, dy) in reference units;
+// ct = cos(pi tau / T) at the stage time.
+struct VelElem {
+  int kind;
+  bool direct;                   // evaluate sinpi/cospi at the point itself (coarse meshes)
+  float x0, y0, hx, hy, ihx, ihy, pihx, pihy;
+  float a, b, om, cx, cy;
+};
+
+__device__ __forceinline__ void vel_at(const VelElem& V, float bx, float by, float Sx, float Cx, float Sy, float Cy,
+                                       float dx, float dy, float ct, float& u, float& v) {
+  switch (V.kind) {
+    case SL_VEL_ROTATION: {
+      const float x = fmaf(V.hx, bx + dx, V.x0), y = fmaf(V.hy, by + dy, V.y0);
+      u = -V.om * (y - V.cy) * V.ihx;
+      v = V.om * (x - V.cx) * V.ihy;
       break;
+    }
     case SL_VEL_SWIRL: {
-      const float c = cospif(tT);
-      const float sx = sinpif(x), sy = sinpif(y);
-      u = sx * sx * sinpif(2.0f * y) * c * X.ihx;
-      v = -sy * sy * sinpif(2.0f * x) * c * X.ihy;
+      float sx, cx, sy, cy;
+      if (V.direct) {
+        sincospif(fmaf(V.hx, bx + dx, V.x0), &sx, &cx);
+        sincospif(fmaf(V.hy, by + dy, V.y0), &sy, &cy);
+      } else {
+        float st, ctt;
+        small_sincos(V.pihx * dx, st, ctt);
+        sx = fmaf(Sx, ctt, Cx * st);
+        cx = fmaf(Cx, ctt, -Sx * st);
+        small_sincos(V.pihy * dy, st, ctt);
+        sy = fmaf(Sy, ctt, Cy * st);
+        cy = fmaf(Cy, ctt, -Sy * st);
+      }
+      // sin(2 pi y) = 2 sin(pi y) cos(pi y)
+      u = sx * sx * (2.0f * sy * cy) * ct * V.ihx;
+      v = -sy * sy * (2.0f * sx * cx) * ct * V.ihy;
       break;
     }
     default:
-      u = X.a * X.ihx;
-      v = X.b * X.ihy;
+      u = V.a * V.ihx;
+      v = V.b * V.ihy;
   }
 }
 
-// One RK step of the displacement (dx, dy), in reference coordinates, of the point (bx, by) of
-// the element with origin (x0, y0); tT = t / T (swirl), h = step in time, hT = h / T.  The
-// displacement is integrated by itself (not the position), so that its float rounding is
-// relative to the displacement and not to the coordinate.
-__device__ __forceinline__ void rk_disp(const StepParams& P, const Mixed2DExtra& X, float x0, float y0, float bx,
-                                        float by, float& dx, float& dy, float tT, float h, float hT) {
-  const int S = c_rk_s[P.rk];
+// One RK step of the displacement (dx, dy) of a point over a time step h (negative: backward), the
+// stage time of stage s being the step fraction f0 + c_s fstep (one of 0, 1/4, 1/2, 3/4, 1, whose
+// cos(pi tau / T) are ctab[0..4]).  The displacement is integrated by itself (not the position), so
+// that its float rounding is relative to the displacement.
+__device__ __forceinline__ void rk_disp(const VelElem& V, int rk, float bx, float by, float Sx, float Cx, float Sy,
+                                        float Cy, float& dx, float& dy, float h, float f0, float fstep,
+                                        const float* ctab) {
+  const int S = c_rk_s[rk];
   float kx[4], ky[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
@@ -108,18 +269,19 @@ __device__ __forceinline__ void rk_disp(const StepParams& P, const Mixed2DExtra&
       float xs = dx, ys = dy;
 #pragma unroll
       for (int j = 0; j < s; ++j) {
-        xs = fmaf(h * c_rk_a[P.rk][s][j], kx[j], xs);
-        ys = fmaf(h * c_rk_a[P.rk][s][j], ky[j], ys);
+        xs = fmaf(h * c_rk_a[rk][s][j], kx[j], xs);
+        ys = fmaf(h * c_rk_a[rk][s][j], ky[j], ys);
       }
-      vel_ref(P, X, fmaf(X.hx, bx + xs, x0), fmaf(X.hy, by + ys, y0), fmaf(c_rk_c[P.rk][s], hT, tT), kx[s], ky[s]);
+      const int ci = __float2int_rn(4.0f * fmaf(c_rk_c[rk][s], fstep, f0));
+      vel_at(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ctab[ci], kx[s], ky[s]);
     }
   }
   float sx = 0.0f, sy = 0.0f;
 #pragma unroll
   for (int s = 0; s < 4; ++s)
     if (s < S) {
-      sx = fmaf(c_rk_b[P.rk][s], kx[s], sx);
-      sy = fmaf(c_rk_b[P.rk][s], ky[s], sy);
+      sx = fmaf(c_rk_b[rk][s], kx[s], sx);
+      sy = fmaf(c_rk_b[rk][s], ky[s], sy);
     }
   dx = fmaf(h, sx, dx);
   dy = fmaf(h, sy, dy);
@@ -143,71 +305,62 @@ __device__ __forceinline__ void basis_at(const float* xi, const float* lam, floa
   }
 }
 
-template <int NT>
-__device__ __forceinline__ float block_sum(float v, float* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  __syncthreads();
-  if (ln == 0) red[w] = v;
-  __syncthreads();
-  float s = 0.0f;
-#pragma unroll
-  for (int i = 0; i < NT / 32; ++i) s += red[i];
-  return s;
-}
-
-// two block sums in one pass (each component summed exactly as block_sum would); red holds
-// 2 NT / 32 floats
-template <int NT>
-__device__ __forceinline__ float2 block_sum2(float a, float b, float* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  __syncthreads();
-  if (ln == 0) {
-    red[w] = a;
-    red[NT / 32 + w] = b;
-  }
-  __syncthreads();
-  float sa = 0.0f, sb = 0.0f;
-#pragma unroll
-  for (int i = 0; i < NT / 32; ++i) {
-    sa += red[i];
-    sb += red[NT / 32 + i];
-  }
-  return make_float2(sa, sb);
-}
-
-template <int NT>
-__device__ __forceinline__ float block_max(float v, float* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
-  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  __syncthreads();
-  if (ln == 0) red[w] = v;
-  __syncthreads();
-  float s = 0.0f;
-#pragma unroll
-  for (int i = 0; i < NT / 32; ++i) s = fmaxf(s, red[i]);
-  return s;
-}
-
+// the same at two points at once, in paired float operations (same rounding per point)
 template <int NN>
-struct Shape {
-  static constexpr int ND = NN * NN;
-  static constexpr int NT = ((ND > 4 * NN ? ND : 4 * NN) + 31) / 32 * 32;
-  // resident CTAs asked of the compiler (one element per CTA keeps the SM latency-bound): register
-  // caps of 64 per thread for n <= 9 (a few bytes of spill at most), about 100 for n <= 13, 128
-  // above (a tighter cap spills there and runs slower)
-  static constexpr int MINB = NN <= 9 ? 65536 / (64 * NT) : NN <= 13 ? 65536 / (96 * NT)
-                                                           : (65536 / (128 * NT) > 1 ? 65536 / (128 * NT) : 1);
-  // phase 2 (less register demand): 64 for n <= 9, about 96 above
-  static constexpr int MINB2 = NN <= 9 ? 65536 / (64 * NT) : 65536 / (96 * NT);
-};
+__device__ __forceinline__ void basis_at2(const float* xi, const float* lam, float z0a, float z0b, float dza, float dzb,
+                                          float2* out) {
+  float2 d[NN], pre[NN];
+  const float2 dz = make_float2(dza, dzb);
+#pragma unroll
+  for (int k = 0; k < NN; ++k) d[k] = __fadd2_rn(make_float2(z0a - xi[k], z0b - xi[k]), dz);
+  float2 acc = make_float2(1.0f, 1.0f);
+#pragma unroll
+  for (int k = 0; k < NN; ++k) { pre[k] = acc; acc = __fmul2_rn(acc, d[k]); }
+  float2 suf = make_float2(1.0f, 1.0f);
+#pragma unroll
+  for (int l = NN - 1; l >= 0; --l) {
+    out[l] = __fmul2_rn(__fmul2_rn(make_float2(lam[l], lam[l]), pre[l]), suf);
+    suf = __fmul2_rn(suf, d[l]);
+  }
+}
+
+// sum_l row[l] b[l] for two vectors b at once (paired FMAs), row 16-byte aligned with NN values
+template <int NN>
+__device__ __forceinline__ float2 row_dot2(const float* row, const float2 (&b)[NN]) {
+  const float4* rowp = reinterpret_cast<const float4*>(row);
+  float2 r = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int q = 0; q < (NN + 3) / 4; ++q) {
+    const float4 v = rowp[q];
+    if (4 * q + 0 < NN) r = __ffma2_rn(make_float2(v.x, v.x), b[(4 * q + 0) % NN], r);
+    if (4 * q + 1 < NN) r = __ffma2_rn(make_float2(v.y, v.y), b[(4 * q + 1) % NN], r);
+    if (4 * q + 2 < NN) r = __ffma2_rn(make_float2(v.z, v.z), b[(4 * q + 2) % NN], r);
+    if (4 * q + 3 < NN) r = __ffma2_rn(make_float2(v.w, v.w), b[(4 * q + 3) % NN], r);
+  }
+  return r;
+}
+
+// sum_l row[l] b[l] for one vector b: even and odd columns in the two lanes of paired FMAs
+template <int NN>
+__device__ __forceinline__ float row_dot(const float* row, const float (&b)[NN]) {
+  const float4* rowp = reinterpret_cast<const float4*>(row);
+  float2 r2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int q = 0; q < NN / 4; ++q) {
+    const float4 v = rowp[q];
+    r2 = __ffma2_rn(make_float2(v.x, v.y), make_float2(b[4 * q], b[4 * q + 1]), r2);
+    r2 = __ffma2_rn(make_float2(v.z, v.w), make_float2(b[4 * q + 2], b[4 * q + 3]), r2);
+  }
+  float r = r2.x + r2.y;
+  if (NN % 4 != 0) {
+    const float4 v = rowp[NN / 4];
+    constexpr int l0 = NN & ~3;
+    r = fmaf(v.x, b[l0], r);
+    if (NN % 4 > 1) r = fmaf(v.y, b[(l0 + 1) % NN], r);
+    if (NN % 4 > 2) r = fmaf(v.z, b[(l0 + 2) % NN], r);
+  }
+  return r;
+}
 
 // per-problem float parameters of a batch element (the FP64 geometry is already in P)
 __device__ __forceinline__ void batch_extra(const StepParams& P, const Map2D& M, Mixed2DExtra& X) {
@@ -217,7 +370,10 @@ __device__ __forceinline__ void batch_extra(const StepParams& P, const Map2D& M,
   X.ihx = (float)(1.0 / P.hx);
   X.ihy = (float)(1.0 / P.hy);
   X.dt = (float)P.dt;
-  X.dt_area = (float)(P.dt / (P.hx * P.hy));
+  const double lam = P.dt / (P.hx * P.hy);
+  X.dt_area = (float)lam;
+  X.lam_hi = (float)lam;
+  X.lam_lo = (float)(lam - (double)X.lam_hi);
   if (X.Tper != 0.0) {
     X.tT = (float)(P.t / X.Tper);
     X.dtT = (float)(P.dt / X.Tper);
@@ -228,423 +384,714 @@ __device__ __forceinline__ int nb_index(const StepParams& P, int ex, int ey, int
   int jx = ex + (face == 0 ? -1 : face == 1 ? 1 : 0);
   int jy = ey + (face == 2 ? -1 : face == 3 ? 1 : 0);
   if (jx >= 0 && jx < P.kx && jy >= 0 && jy < P.ky) return jy * P.kx + jx;
-  if (P.bc[face] != SL_BC_PERIODIC) return -1;
+  // the face's boundary condition by selection (a dynamic index would put P in local memory)
+  const int bc = face == 0 ? P.bc[0] : face == 1 ? P.bc[1] : face == 2 ? P.bc[2] : P.bc[3];
+  if (bc != SL_BC_PERIODIC) return -1;
   jx = (jx + P.kx) % P.kx;
   jy = (jy + P.ky) % P.ky;
   return jy * P.kx + jx;
 }
 
-// element reference L = r0 + gx (xi - 1/2) + gy (eta - 1/2) in double
-__device__ __forceinline__ double lref(float r0, float gx, float gy, double xi, double eta) {
-  return (double)r0 + (double)gx * (xi - 0.5) + (double)gy * (eta - 0.5);
+// the element of launch-list index k; copies its problem's geometry and step into P (batches)
+template <int NN>
+__device__ __forceinline__ Elem elem_at(StepParams& P, const Map2D& M, int64_t k) {
+  Elem E;
+  E.g = M.list ? (int64_t)M.list[k] : k;
+  E.gb = 0;
+  if (M.geo) {
+    const ProbGeom& G = M.geo[M.prob[E.g]];
+    P.kx = G.kx;
+    P.ky = G.ky;
+    for (int f = 0; f < 4; ++f) P.bc[f] = G.bc[f];
+    P.x0 = G.x0;
+    P.hx = G.hx;
+    P.y0 = G.y0;
+    P.hy = G.hy;
+    P.ghost = G.ghost;
+    P.t = G.t;
+    P.dt = G.dt;
+    E.gb = G.gbase;
+  }
+  E.e = (int)(E.g - E.gb);
+  E.ex = E.e % P.kx;
+  E.ey = E.e / P.kx;
+  E.base = M.off ? M.off[E.g] : E.g * (NN * NN);
+  return E;
 }
 
+__device__ __forceinline__ VelElem make_vel(const StepParams& P, const Mixed2DExtra& X, float x0, float y0) {
+  VelElem V;
+  V.kind = P.vel_kind;
+  V.x0 = x0;
+  V.y0 = y0;
+  V.hx = X.hx;
+  V.hy = X.hy;
+  V.ihx = X.ihx;
+  V.ihy = X.ihy;
+  V.pihx = 3.14159265358979f * X.hx;
+  V.pihy = 3.14159265358979f * X.hy;
+  V.direct = !(X.hx <= 0.25f && X.hy <= 0.25f);
+  V.a = X.a;
+  V.b = X.b;
+  V.om = X.om;
+  V.cx = X.cx;
+  V.cy = X.cy;
+  return V;
+}
+
+// Per-element sines and cosines of the swirl: sin and cos of pi x at the node x-coordinates n[0],
+// n[1], y-coordinates n[2], n[3]; at the corner coordinates x0, x0 + hx, y0, y0 + hy (sines in
+// corner[0..3], cosines in corner[4..7]); ct[k] = cos(pi (t + k dt / 4) / T).
 template <int NN>
-__global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB) k_p1(StepParams P0, const __grid_constant__ Mixed2DExtra X0,
-                                                     Map2D M, const float* __restrict__ in, Work2M W,
-                                                     unsigned* status) {
-  constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
+struct Trig {
+  float n[4][NN];
+  float corner[8];
+  float ct[5];
+};
+
+template <int NN, int G>
+__device__ __forceinline__ void trig_setup(const Grp<G>& g, const VelElem& V, const Mixed2DExtra& X, const float* xi,
+                                           Trig<NN>& T) {
+  const int t = g.t;
+  if (V.kind == SL_VEL_SWIRL) {
+    if (t < NN) sincospif(fmaf(V.hx, xi[t], V.x0), &T.n[0][t], &T.n[1][t]);
+    else if (t < 2 * NN) sincospif(fmaf(V.hy, xi[t - NN], V.y0), &T.n[2][t - NN], &T.n[3][t - NN]);
+    else if (t < 2 * NN + 4) {
+      const int k = t - 2 * NN;
+      const float z = k < 2 ? V.x0 + (k == 1 ? V.hx : 0.0f) : V.y0 + (k == 3 ? V.hy : 0.0f);
+      sincospif(z, &T.corner[k], &T.corner[4 + k]);
+    } else if (t < 2 * NN + 9) {
+      const int k = t - 2 * NN - 4;
+      T.ct[k] = cospif(fmaf(0.25f * (float)k, X.dtT, X.tT));
+    }
+  } else if (t < 5) {
+    T.ct[t] = 1.0f;
+  }
+}
+
+// ------------------------------------------------------------------ phase 1
+template <int NN>
+struct Smem1 {
+  static constexpr int ND = Shape<NN>::ND, NP = Shape<NN>::NP, RS = Shape<NN>::RS, G = Shape<NN>::G;
+  __align__(16) float ph[NN * NP];             // psihat rows
+  __align__(16) float psi[NN * NP];            // psi^n rows
+  float r[ND], tt[ND], best[ND];
+  float Rx[NN * RS], Ry[NN * RS];
+  float fp[4][NMAX][4];                        // per face point: U_out, U_in, P1, P2
+  float red[4 * G];
+  int cum[5];
+  Trig<NN> T;
+};
+
+template <int NN>
+__global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
+    k_p1(StepParams P0, const __grid_constant__ Mixed2DExtra X0, Map2D M, int64_t count, const float* __restrict__ in,
+         Work2M W, unsigned* status) {
+  using S = Shape<NN>;
+  constexpr int ND = S::ND, NP = S::NP, RS = S::RS, G = S::G, GT = S::GT, EPC = S::EPC;
   __shared__ float s_xi[NN], s_lam[NN], s_w[NN], s_l0[NN], s_l1[NN];
-  constexpr int NP = (NN + 3) & ~3;                // psihat rows padded to 16 bytes
-  __shared__ float s_t[ND], s_r[ND], s_Rx[ND], s_Ry[ND];
-  __shared__ __align__(16) float s_psi[NN * NP];   // psi^n rows, padded like psihat
-  __shared__ __align__(16) float s_ph[NN * NP];
-  __shared__ float s_red[NT / 32];
-  __shared__ float s_fs[4][NMAX][3][4];          // face point x distinct stage partial sums
-  __shared__ int s_nq[4];
-  const int tid = threadIdx.x;
-  StepParams P = P0;
-  const Elem E = elem_of<NN>(P, M);
-  Mixed2DExtra X = X0;
-  batch_extra(P, M, X);
-  const int ex = E.ex, ey = E.ey;
-  const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
-  if (tid < NN) {
-    s_xi[tid] = X.xi[tid]; s_lam[tid] = X.lam[tid]; s_w[tid] = X.w[tid];
-    s_l0[tid] = X.l0[tid]; s_l1[tid] = X.l1[tid];
-  }
-  const bool part = tid < ND;
-  const int i = tid % NN, j = tid / NN;
-  // element reference: linear from the four corner values, or the first node value
-  const float c00 = in[E.base], c01 = in[E.base + NN - 1], c10 = in[E.base + (NN - 1) * NN], c11 = in[E.base + ND - 1];
-  float ref = c00, gx = 0.0f, gy = 0.0f;
-  if (X.linref) {
-    const float span = (float)(0.5 / (X.xid[NN - 1] - X.xid[0]));
-    ref = 0.25f * ((c00 + c01) + (c10 + c11));
-    gx = ((c01 + c11) - (c00 + c10)) * span;
-    gy = ((c10 + c11) - (c00 + c01)) * span;
-  }
-  if (part)
-    s_psi[j * NP + i] = (float)(((double)in[E.base + tid] + (double)in[X.plane + E.base + tid]) -
-                         lref(ref, gx, gy, X.xid[i], X.xid[j]));
-  __syncthreads();
-
-  // advect the particle of node (i, j) in reference coordinates
-  float Lx[NN], Ly[NN], ps = 0.0f, pn = 0.0f, dxs = 0.0f, dys = 0.0f;
-  if (part) {
-    float ddx = 0.0f, ddy = 0.0f;
-    rk_disp(P, X, x0, y0, s_xi[i], s_xi[j], ddx, ddy, X.tT, X.dt, X.dtT);
-    basis_at<NN>(s_xi, s_lam, s_xi[i], ddx, Lx);
-    basis_at<NN>(s_xi, s_lam, s_xi[j], ddy, Ly);
-    pn = s_psi[j * NP + i];
-    ps = pn - fmaf(gx, ddx, gy * ddy);       // collocation data of phihat - L
-    dxs = ddx;
-    dys = ddy;
-  }
-  const float mdx = block_sum<NT>(dxs, s_red) / ND;
-  const float mdy = block_sum<NT>(dys, s_red) / ND;
-  if (part) {
-    float b[NN];
-    basis_at<NN>(s_xi, s_lam, s_xi[j], -mdx, b);
-    s_Rx[tid] = b[i];
-    basis_at<NN>(s_xi, s_lam, s_xi[j], -mdy, b);
-    s_Ry[tid] = b[i];
-    s_r[tid] = ps;
+  __shared__ Smem1<NN> sm_all[EPC];
+  if (threadIdx.x < NN) {
+    s_xi[threadIdx.x] = X0.xi[threadIdx.x];
+    s_lam[threadIdx.x] = X0.lam[threadIdx.x];
+    s_w[threadIdx.x] = X0.w[threadIdx.x];
+    s_l0[threadIdx.x] = X0.l0[threadIdx.x];
+    s_l1[threadIdx.x] = X0.l1[threadIdx.x];
   }
   __syncthreads();
-  auto precond_add = [&](bool first) {
-    if (part) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int q = 0; q < NN; ++q) acc = fmaf(s_Rx[i * NN + q], s_r[j * NN + q], acc);
-      s_t[tid] = acc;
+  Grp<G> g;
+  g.slot = threadIdx.x / GT;
+  g.t = threadIdx.x % GT;
+  g.lane = threadIdx.x & 31;
+  g.w = g.t >> 5;
+  Smem1<NN>& sm = sm_all[g.slot];
+  g.red = sm.red;
+  g.rb = 0;
+  const int t = g.t;
+  const int p0 = t, p1 = t + GT;
+  const bool v0 = p0 < ND, v1 = p1 < ND;
+  const int i0 = p0 % NN, j0 = (p0 / NN) % NN, i1 = p1 % NN, j1 = (p1 / NN) % NN;
+  unsigned long long c_it = 0, c_floor = 0, c_nc = 0;
+  unsigned bits = 0;
+  const int64_t ngroups = (int64_t)gridDim.x * EPC;
+  for (int64_t k = (int64_t)blockIdx.x * EPC + g.slot; k < count; k += ngroups) {
+    g.sync();                                    // the previous element's shared data is consumed
+    StepParams P = P0;
+    const Elem E = elem_at<NN>(P, M, k);
+    Mixed2DExtra X = X0;
+    batch_extra(P, M, X);
+    const int ex = E.ex, ey = E.ey;
+    const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
+    const VelElem V = make_vel(P, X, x0, y0);
+    trig_setup<NN>(g, V, X, s_xi, sm.T);
+    // element reference: linear from the four corner values, or the first node value
+    const float c00 = in[E.base], c01 = in[E.base + NN - 1], c10 = in[E.base + (NN - 1) * NN], c11 = in[E.base + ND - 1];
+    float r0 = c00, gx = 0.0f, gy = 0.0f;
+    if (X.linref) {
+      r0 = 0.25f * ((c00 + c01) + (c10 + c11));
+      gx = ((c01 + c11) - (c00 + c10)) * X.span;
+      gy = ((c10 + c11) - (c00 + c01)) * X.span;
     }
-    __syncthreads();
-    if (part) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int q = 0; q < NN; ++q) acc = fmaf(s_Ry[j * NN + q], s_t[q * NN + i], acc);
-      s_ph[j * NP + i] = first ? acc : s_ph[j * NP + i] + acc;
+    // psi^n at the own nodes, and the element mass in float-float
+    float pn0 = 0.0f, pn1 = 0.0f;
+    ff mn = {0.0f, 0.0f};
+    if (v0) {
+      const float hi = in[E.base + p0], lo = in[X.plane + E.base + p0];
+      const ff L = lref(r0, gx, gy, s_xi[i0] - 0.5f, s_xi[j0] - 0.5f);
+      pn0 = __fadd_rn(__fsub_rn(hi, L.hi), __fsub_rn(lo, L.lo));
+      sm.psi[j0 * NP + i0] = pn0;
+      mn = ff_mul(ff{hi, lo}, ff{X.w2h[p0], X.w2l[p0]});
     }
-    __syncthreads();
-  };
-  precond_add(true);
-  const float scale = block_max<NT>(part ? fabsf(ps) : 0.0f, s_red);
-  // Stop at the tolerance, or once the residual has stalled at the float floor; guard against
-  // divergence by keeping the best iterate.
-  bool solved = false;
-  float prev = INFINITY, best = INFINITY;
-  __shared__ float s_best[ND];
-  for (int it = 0; it < SOLVE_CAP; ++it) {
-    float r = 0.0f;
-    if (part) {
-      // row sums: every thread reads the same psihat row
-      float acc = 0.0f;
-#pragma unroll 1
+    if (v1) {
+      const float hi = in[E.base + p1], lo = in[X.plane + E.base + p1];
+      const ff L = lref(r0, gx, gy, s_xi[i1] - 0.5f, s_xi[j1] - 0.5f);
+      pn1 = __fadd_rn(__fsub_rn(hi, L.hi), __fsub_rn(lo, L.lo));
+      sm.psi[j1 * NP + i1] = pn1;
+      mn = ff_add(mn, ff_mul(ff{hi, lo}, ff{X.w2h[p1], X.w2l[p1]}));
+    }
+    g.sync();
+    // advect the particles of nodes p0, p1 in reference coordinates
+    float dx0 = 0.0f, dy0 = 0.0f, dx1 = 0.0f, dy1 = 0.0f;
+    if (v0)
+      rk_disp(V, P.rk, s_xi[i0], s_xi[j0], sm.T.n[0][i0], sm.T.n[1][i0], sm.T.n[2][j0], sm.T.n[3][j0], dx0, dy0, X.dt,
+              0.0f, 1.0f, sm.T.ct);
+    if (v1)
+      rk_disp(V, P.rk, s_xi[i1], s_xi[j1], sm.T.n[0][i1], sm.T.n[1][i1], sm.T.n[2][j1], sm.T.n[3][j1], dx1, dy1, X.dt,
+              0.0f, 1.0f, sm.T.ct);
+    float2 Lx[NN], Ly[NN];
+    basis_at2<NN>(s_xi, s_lam, s_xi[i0], s_xi[i1], dx0, dx1, Lx);
+    basis_at2<NN>(s_xi, s_lam, s_xi[j0], s_xi[j1], dy0, dy1, Ly);
+    // collocation data of psihat = phihat - L
+    const float ps0 = v0 ? pn0 - fmaf(gx, dx0, gy * dy0) : 0.0f;
+    const float ps1 = v1 ? pn1 - fmaf(gx, dx1, gy * dy1) : 0.0f;
+    const float2 md = g.sum2(dx0 + dx1, dy0 + dy1);
+    const float mdx = md.x / ND, mdy = md.y / ND;
+    // preconditioner: interpolation back over the mean displacement, Rx[i][q] = l_q(xi_i - mdx)
+    if (t < 2 * NN) {
+      float b[NN];
+      const int row = t < NN ? t : t - NN;
+      basis_at<NN>(s_xi, s_lam, s_xi[row], t < NN ? -mdx : -mdy, b);
+      float* R = (t < NN ? sm.Rx : sm.Ry) + row * RS;
+#pragma unroll
+      for (int q = 0; q < NN; ++q) R[q] = b[q];
+    }
+    if (v0) sm.r[p0] = ps0;
+    if (v1) sm.r[p1] = ps1;
+    g.sync();
+    // psihat (+)= Ry r Rx^T
+    auto precond = [&](bool first) {
+      if (v0) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) acc = fmaf(sm.Rx[i0 * RS + q], sm.r[j0 * NN + q], acc);
+        sm.tt[p0] = acc;
+      }
+      if (v1) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) acc = fmaf(sm.Rx[i1 * RS + q], sm.r[j1 * NN + q], acc);
+        sm.tt[p1] = acc;
+      }
+      g.sync();
+      if (v0) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) acc = fmaf(sm.Ry[j0 * RS + q], sm.tt[q * NN + i0], acc);
+        sm.ph[j0 * NP + i0] = first ? acc : sm.ph[j0 * NP + i0] + acc;
+      }
+      if (v1) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) acc = fmaf(sm.Ry[j1 * RS + q], sm.tt[q * NN + i1], acc);
+        sm.ph[j1 * NP + i1] = first ? acc : sm.ph[j1 * NP + i1] + acc;
+      }
+      g.sync();
+    };
+    precond(true);
+    const float scale = g.max(fmaxf(fabsf(ps0), fabsf(ps1)));
+    // iterate to the tolerance; a residual that stalls at the float floor is accepted; the best
+    // iterate is kept against divergence, and accepting it above the floor is reported
+    float prev = INFINITY, best = INFINITY, rmax = INFINITY;
+    int it = 0;
+    bool done = false;
+    for (; it < SOLVE_CAP; ++it) {
+      float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
       for (int mm = 0; mm < NN; ++mm) {
-        const float row = row_dot<NN>(s_ph + mm * NP, Lx);
-        acc = fmaf(Ly[mm], row, acc);
+        const float2 row = row_dot2<NN>(sm.ph + mm * NP, Lx);
+        acc = __ffma2_rn(Ly[mm], row, acc);
       }
-      r = ps - acc;
-      s_r[tid] = r;
-    }
-    const float rmax = block_max<NT>(fabsf(r), s_red);
-    // values below the normal float range carry no accuracy to refine
-    if (rmax <= SOLVE_RTOL * scale || rmax == 0.0f || scale < 1e-30f) { solved = true; break; }
-    const bool stalled = rmax > 0.5f * prev && rmax <= SOLVE_STALL * scale;   // at the float floor
-    const bool diverging = !(rmax <= 4.0f * best);                             // or not finite
-    if (stalled || diverging) {
-      if (!(rmax <= best)) {                  // back to the best iterate
-        if (part) s_ph[j * NP + i] = s_best[tid];
-        __syncthreads();
+      const float r0v = ps0 - acc.x, r1v = ps1 - acc.y;
+      rmax = g.max(fmaxf(v0 ? fabsf(r0v) : 0.0f, v1 ? fabsf(r1v) : 0.0f));
+      // values below the normal float range carry no accuracy to refine
+      if (rmax <= SOLVE_RTOL * scale || rmax == 0.0f || scale < 1e-30f) { done = true; break; }
+      const bool stalled = rmax > 0.5f * prev && rmax <= SOLVE_STALL * scale;
+      const bool diverging = !(rmax <= 4.0f * best);                             // or not finite
+      if (stalled || diverging) break;
+      if (rmax < best) {
+        best = rmax;
+        if (v0) sm.best[p0] = sm.ph[j0 * NP + i0];
+        if (v1) sm.best[p1] = sm.ph[j1 * NP + i1];
       }
-      solved = fminf(rmax, best) <= SOLVE_FLOOR * scale;
-      break;
+      prev = rmax;
+      if (v0) sm.r[p0] = r0v;
+      if (v1) sm.r[p1] = r1v;
+      g.sync();
+      precond(false);
     }
-    if (rmax < best) {
-      best = rmax;
-      if (part) s_best[tid] = s_ph[j * NP + i];
-    }
-    prev = rmax;
-    precond_add(false);
-  }
-  if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);
-  if (part) W.psihat[E.base + tid] = s_ph[j * NP + i];
-  // element sums of psi^n (reference measure)
-  const float w2 = part ? s_w[i] * s_w[j] : 0.0f;
-  const float m1 = block_sum<NT>(w2 * pn, s_red);
-  const float m2 = block_sum<NT>(w2 * pn * pn, s_red);
-  if (tid == 0) {
-    W.elem[E.g * 8 + 0] = ref;
-    W.elem[E.g * 8 + 1] = gx;
-    W.elem[E.g * 8 + 2] = gy;
-    W.elem[E.g * 8 + 3] = m1;
-    W.elem[E.g * 8 + 4] = m2;
-  }
-  // traces of psihat (relative to ref)
-  if (tid < 4 * NN) {
-    const int f = tid / NN, q = tid % NN;
-    const float* L = (f == 1 || f == 3) ? s_l1 : s_l0;
-    float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < NN; ++k) acc = fmaf(f < 2 ? s_ph[q * NP + k] : s_ph[k * NP + q], L[k], acc);
-    W.traces[E.g * M.tstride + tid] = acc;
-  }
-  // face sums over the step; a face shared with a neighbour of another node count takes the rule
-  // of the finer side, so that both elements integrate the same points
-  if (P.cons & (SL_C_MASS | SL_C_ENERGY)) {
-    if (tid < 4) {
-      const int nb = nb_index(P, ex, ey, tid);
-      s_nq[tid] = nb < 0 ? NN : max(NN, order_of<NN>(M, E.gb + nb));
-    }
-    __syncthreads();
-    // one work item per (face, point, distinct stage time), partial sums kept per item and added
-    // in a fixed order below
-    const int S = c_ds_n[P.rk];
-    for (int idx = tid; idx < 4 * NMAX * 3; idx += NT) {
-      const int f = idx / (NMAX * 3), q = (idx / 3) % NMAX, s = idx % 3;
-      const int nq = s_nq[f];
-      if (q >= nq || s >= S) continue;
-      const float* rule = X.rules + (size_t)nq * 3 * NMAX;
-      const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : rule[q];
-      const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : rule[q];
-      const float hn = f < 2 ? X.hx : X.hy;          // velocity in reference units times this = u.n
-      const float sg = (f == 0 || f == 2) ? -1.0f : 1.0f;
-      const float Wq = (f < 2 ? X.hy : X.hx) * rule[2 * NMAX + q];
-      float uo = 0.0f, ui = 0.0f, p1 = 0.0f, p2 = 0.0f;
-      const float cs = c_ds_c[P.rk][s];
-      float ur, vr;
-      vel_ref(P, X, fmaf(X.hx, xr, x0), fmaf(X.hy, yr, y0), fmaf(cs, X.dtT, X.tT), ur, vr);
-      const float un = sg * (f < 2 ? ur : vr) * hn;
-      const float bw = c_ds_b[P.rk][s] * Wq * un;
-      if (un > (float)TIE) {
-        uo = bw;
-        float fdx = 0.0f, fdy = 0.0f;
-        if (cs != 0.0f) rk_disp(P, X, x0, y0, xr, yr, fdx, fdy, fmaf(cs, X.dtT, X.tT), -cs * X.dt, -cs * X.dtT);
-        float bx[NN], by[NN];
-        basis_at<NN>(s_xi, s_lam, xr, fdx, bx);
-        basis_at<NN>(s_xi, s_lam, yr, fdy, by);
-        float val = 0.0f;
-#pragma unroll 1
-        for (int mm = 0; mm < NN; ++mm) val = fmaf(by[mm], row_dot<NN>(s_psi + mm * NP, bx), val);
-        val += fmaf(gx, (xr - 0.5f) + fdx, gy * ((yr - 0.5f) + fdy));   // phi - r0 = (L - r0) + psi
-        p1 = bw * val;
-        p2 = p1 * val;
-      } else if (un < -(float)TIE) {
-        ui = bw;
+    c_it += (unsigned long long)(it < SOLVE_CAP ? it + 1 : SOLVE_CAP);
+    if (!done) {
+      // stalled, diverging or at the cap: the better of the last and the best iterate
+      float acc_r = rmax;
+      if (!(rmax <= best)) {
+        if (v0) sm.ph[j0 * NP + i0] = sm.best[p0];
+        if (v1) sm.ph[j1 * NP + i1] = sm.best[p1];
+        acc_r = best;
+        g.sync();
       }
-      s_fs[f][q][s][0] = uo; s_fs[f][q][s][1] = ui; s_fs[f][q][s][2] = p1; s_fs[f][q][s][3] = p2;
-    }
-    __syncthreads();
-    if (tid < 16) {
-      const int f = tid >> 2, k = tid & 3;
-      float acc = 0.0f;
-      for (int q = 0; q < s_nq[f]; ++q)
-        for (int s = 0; s < S; ++s) acc += s_fs[f][q][s][k];
-      W.faces[E.g * 16 + tid] = acc;
-    }
-  }
-}
-
-template <int NN>
-__global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2) k_p2(StepParams P0, const __grid_constant__ Mixed2DExtra X0,
-                                                     Map2D M, const float* __restrict__ in, Work2M W,
-                                                     float* __restrict__ out, unsigned* status) {
-  constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
-  constexpr int MMAX = 4 * NN + 1;
-  __shared__ float s_xi[NN], s_w[NN], s_l0[NN], s_l1[NN];
-  __shared__ float s_ph[ND], s_a[ND];
-  __shared__ float s_r[MMAX], s_ca[MMAX];
-  __shared__ float s_red[NT / 32];
-  __shared__ float s_red2[2 * (NT / 32)];
-  __shared__ float s_scal[4];
-  const int tid = threadIdx.x;
-  StepParams P = P0;
-  const Elem E = elem_of<NN>(P, M);
-  Mixed2DExtra X = X0;
-  batch_extra(P, M, X);
-  const int ex = E.ex, ey = E.ey;
-  const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
-  const float tn1T = X.tT + X.dtT;
-  if (tid < NN) { s_xi[tid] = X.xi[tid]; s_w[tid] = X.w[tid]; s_l0[tid] = X.l0[tid]; s_l1[tid] = X.l1[tid]; }
-  const bool part = tid < ND;
-  const int i = tid % NN, j = tid / NN;
-  const float ref = W.elem[E.g * 8], gx = W.elem[E.g * 8 + 1], gy = W.elem[E.g * 8 + 2];
-  float ph = 0.0f;
-  if (part) {
-    ph = W.psihat[E.base + tid];
-    s_ph[tid] = ph;
-  }
-  __syncthreads();
-  const float w2 = part ? s_w[i] * s_w[j] : 0.0f;
-  const bool bnd = (P.cons & SL_C_BOUNDARY) != 0;
-  const int nb_rows = bnd ? 4 * NN : 0;
-  if (bnd && tid < 4 * NN) {
-    const int f = tid / NN, q = tid % NN;
-    const int nb = nb_index(P, ex, ey, f);
-    const float own = W.traces[E.g * M.tstride + tid];
-    // neighbour's value at this element's face points, relative to this element's reference L:
-    // (L_nb - L) in double (it is of the size of psi when both references fit the same data), plus
-    // the neighbour's trace of its own psihat
-    const double xq = X.xid[q];
-    const double fx = f == 0 ? 0.0 : f == 1 ? 1.0 : xq, fy = f == 2 ? 0.0 : f == 3 ? 1.0 : xq;
-    const double lown = lref(ref, gx, gy, fx, fy);
-    float other = (float)(P.ghost - lown);
-    if (nb >= 0) {
-      const int64_t gn = E.gb + nb;
-      const int nn = order_of<NN>(M, gn);
-      const float* tr = W.traces + gn * M.tstride + (f ^ 1) * nn;
-      const float* en = W.elem + gn * 8;
-      const double lnb = lref(en[0], en[1], en[2], f == 0 ? 1.0 : f == 1 ? 0.0 : fx, f == 2 ? 1.0 : f == 3 ? 0.0 : fy);
-      other = (float)(lnb - lown) + (nn == NN ? tr[q] : interp_rule(X.rules, nn, tr, s_xi[q]));
-    }
-    const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : s_xi[q];
-    const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : s_xi[q];
-    float ur, vr;
-    vel_ref(P, X, fmaf(X.hx, xr, x0), fmaf(X.hy, yr, y0), tn1T, ur, vr);
-    const float un = (f == 0 || f == 2 ? -1.0f : 1.0f) * (f < 2 ? ur * X.hx : vr * X.hy);
-    float val;
-    if (un > (float)TIE) val = own;
-    else if (un < -(float)TIE) val = other;
-    else val = nb < 0 ? own : 0.5f * (own + other);
-    s_r[tid] = val - own;
-  }
-  const bool mass = (P.cons & SL_C_MASS) != 0, energy = (P.cons & SL_C_ENERGY) != 0;
-  float netm = 0.0f, netd2 = 0.0f, nu = 0.0f;
-  if ((mass || energy) && tid < 32) {
-    // net outflow of mass (increments) and of the squared increments, plus the velocity balance:
-    // lanes 0-3 of the first warp take one face each, summed in face order
-    float cu = 0.0f, cm = 0.0f, cd = 0.0f;
-    if (tid < 4) {
-      const int f = tid;
-      const float* F = W.faces + E.g * 16 + 4 * f;
-      const int nb = nb_index(P, ex, ey, f);
-      cu = F[0] + F[1];
-      if (nb >= 0) {
-        const float* G = W.faces + (E.gb + nb) * 16 + 4 * (f ^ 1);
-        const float dref = W.elem[(E.gb + nb) * 8] - ref;
-        // inflow part: u.n (dref + psi_nb) with the neighbour's u.n = -ours
-        cm = F[2] + (dref * F[1] - G[2]);
-        cd = F[3] + (dref * dref * F[1] - 2.0f * dref * G[2] - G[3]);
+      if (acc_r <= SOLVE_STALL * scale) {
+        // the float floor of the residual: the solve is as accurate as float allows
+      } else if (acc_r <= SOLVE_FLOOR * scale) {
+        ++c_floor;
+        bits |= SL_ST_SOLVE_FLOOR;
       } else {
-        const float g = (float)(P.ghost - (double)ref);
-        cm = F[2] + g * F[1];
-        cd = F[3] + g * g * F[1];
+        ++c_nc;
+        bits |= SL_ST_SOLVE_NOCONV;
       }
     }
-    float su = 0.0f, sm = 0.0f, sd = 0.0f;
+    if (v0) W.psihat[E.base + p0] = sm.ph[j0 * NP + i0];
+    if (v1) W.psihat[E.base + p1] = sm.ph[j1 * NP + i1];
+    // element sums of psi^n (reference measure) and the float-float element mass
+    const float w20 = v0 ? s_w[i0] * s_w[j0] : 0.0f, w21 = v1 ? s_w[i1] * s_w[j1] : 0.0f;
+    const float2 m12 = g.sum2(fmaf(w20, pn0, w21 * pn1), fmaf(w20 * pn0, pn0, w21 * pn1 * pn1));
+    const ff Mn = g.ffsum(mn);
+    float* el = W.elem + E.g * 8;
+    if (t == 0) {
+      el[0] = r0;
+      el[1] = gx;
+      el[2] = gy;
+      el[3] = m12.x;
+      el[4] = m12.y;
+      el[5] = Mn.hi;
+      el[6] = Mn.lo;
+    }
+    // traces of psihat (relative to L)
+    if (t < 4 * NN) {
+      const int f = t / NN, q = t % NN;
+      const float* Lb = (f == 1 || f == 3) ? s_l1 : s_l0;
+      float acc = 0.0f;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      su += __shfl_sync(0xffffffffu, cu, f);
-      sm += __shfl_sync(0xffffffffu, cm, f);
-      sd += __shfl_sync(0xffffffffu, cd, f);
+      for (int kk = 0; kk < NN; ++kk) acc = fmaf(f < 2 ? sm.ph[q * NP + kk] : sm.ph[kk * NP + q], Lb[kk], acc);
+      W.traces[E.g * M.tstride + t] = acc;
     }
-    if (tid == 0) {
-      s_scal[0] = sm;
-      s_scal[1] = sd;
-      s_scal[2] = su;
-    }
-  }
-  __syncthreads();
-  netm = s_scal[0];
-  netd2 = s_scal[1];
-  nu = s_scal[2];
-  const float lam = X.dt_area;               // dt / (hx hy)
-  if (mass) {
-    const float mh = block_sum<NT>(w2 * ph, s_red);
-    // target (increments): sum w psi^n - lam (net increment outflow + ref * closed-surface u.n)
-    // ref * (closed-surface integral of u.n) is dropped: every 2D velocity here is divergence free
-    // and the face quadrature integrates it to rounding; in float it would be noise of eps |U|
-    if (tid == 0) s_r[nb_rows] = (W.elem[E.g * 8 + 3] - lam * netm) - mh;
-  }
-  __syncthreads();
-  const int m = P.m;
-  float phL = ph;
-  if (part) {
-    float acc = ph;
-    for (int k = 0; k < m; ++k) acc = fmaf(X.Cp[(size_t)k * ND + tid], s_r[k], acc);
-    phL = acc;
-  }
-  float cur = phL;
-  bool ok = true;
-  if (energy) {
-    // energy mismatch from increments (mass enforced): sum w (psiL - psi)(psiL + psi) + lam net(delta^2);
-    // without the mass row, add 2 ref times the mass residual (closed-surface u.n taken as zero)
-    const float psin = part ? (float)(((double)in[E.base + tid] + (double)in[X.plane + E.base + tid]) -
-                                      lref(ref, gx, gy, X.xid[i], X.xid[j]))
-                            : 0.0f;
-    const float dpsi = part ? phL - psin : 0.0f;
-    const float2 evml = block_sum2<NT>(w2 * dpsi * (phL + (phL - dpsi)), w2 * phL, s_red2);
-    const float ev = evml.x, ml = evml.y;
-    const float m1 = W.elem[E.g * 8 + 3];
-    float gamma;
-    if (mass) gamma = ev + lam * netd2;
-    else gamma = fmaf(2.0f * ref, (ml - m1) + lam * netm, ev + lam * netd2);
-    const float escale = block_sum<NT>(part ? w2 * (ref + cur) * (ref + cur) : 0.0f, s_red);
-    float smax = block_max<NT>(part ? fmaxf(fabsf(phL), fabsf(ref)) : 0.0f, s_red);
-    if (smax >= 1e-30f && fabsf(gamma) > (float)ENERGY_SKIP_RTOL_MIXED * escale) {
-      int exn;
-      frexpf(smax, &exn);
-      const float sc = ldexpf(1.0f, -exn), usc = ldexpf(1.0f, exn);
-      const float rf = ref * sc, gm = gamma * sc * sc;
-      const float ql = phL * sc;
-      float c2 = ql;
-      const float tol = 2.4e-7f * 1.0f + 1e-30f;   // scaled units: values are of order one
-      bool conv = false, feasible = true;
-      for (int it = 0; it < P.picard_cap; ++it) {
-        const float a = w2 * (mass ? c2 : rf + c2);
-        if (part) s_a[tid] = a;
-        __syncthreads();
-        if (bnd && tid < 4 * NN) {
-          const int f = tid / NN, qq = tid % NN;
-          const float* L = (f == 1 || f == 3) ? s_l1 : s_l0;
-          float acc = 0.0f;
-          for (int k = 0; k < NN; ++k) acc = fmaf(f < 2 ? s_a[qq * NN + k] : s_a[k * NN + qq], L[k], acc);
-          s_ca[tid] = acc;
+    // outflow over each face and step; a face shared with a neighbour of another node count takes
+    // the rule of the finer side, so that both elements integrate the same points
+    if (P.cons & (SL_C_MASS | SL_C_ENERGY)) {
+      if (t == 0) {
+        int acc = 0;
+        sm.cum[0] = 0;
+        for (int f = 0; f < 4; ++f) {
+          const int nb = nb_index(P, ex, ey, f);
+          acc += nb < 0 ? NN : max(NN, order_of<NN>(M, E.gb + nb));
+          sm.cum[f + 1] = acc;
         }
-        if (mass) {
-          const float cm = block_sum<NT>(w2 * a, s_red);
-          if (tid == 0) s_ca[nb_rows] = cm;
-        }
-        __syncthreads();
-        float q = 0.0f;
-        if (part) {
-          float acc = a;
-          for (int k = 0; k < m; ++k) acc = fmaf(-X.Cp[(size_t)k * ND + tid], s_ca[k], acc);
-          q = acc;
-        }
-        const float2 ab = block_sum2<NT>(w2 * ql * q, w2 * q * q, s_red2);
-        float alpha = ab.x;
-        if (!mass) alpha = fmaf(rf, block_sum<NT>(w2 * q, s_red), alpha);
-        const float beta = ab.y;
-        float s;
-        if (beta <= 0.0f) { s = 0.0f; feasible = gm <= 0.0f; }
-        else {
-          const float disc = alpha * alpha - beta * gm;
-          if (disc < 0.0f) { s = -alpha / beta; feasible = false; }
-          else {
-            const float root = sqrtf(disc);
-            const float den = alpha + (alpha >= 0.0f ? root : -root);
-            s = den == 0.0f ? 0.0f : -gm / den;
-            feasible = true;
+      }
+      g.sync();
+      const int S = c_ds_n[P.rk];
+      const int total = sm.cum[4];
+      for (int idx = t; idx < total; idx += GT) {
+        const int f = (idx >= sm.cum[1]) + (idx >= sm.cum[2]) + (idx >= sm.cum[3]);
+        const int q = idx - sm.cum[f];
+        const int nq = sm.cum[f + 1] - sm.cum[f];
+        const float* rule = X.rules + (size_t)nq * 3 * NMAX;
+        const float zq = nq == NN ? s_xi[q] : rule[q];
+        const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : zq;
+        const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : zq;
+        // sines and cosines at the face point (swirl)
+        float Sx = 0.0f, Cx = 0.0f, Sy = 0.0f, Cy = 0.0f;
+        if (V.kind == SL_VEL_SWIRL && !V.direct) {
+          if (f < 2) {
+            Sx = sm.T.corner[f];
+            Cx = sm.T.corner[4 + f];
+            if (nq == NN) { Sy = sm.T.n[2][q]; Cy = sm.T.n[3][q]; }
+            else sincospif(fmaf(V.hy, zq, V.y0), &Sy, &Cy);
+          } else {
+            Sy = sm.T.corner[f];
+            Cy = sm.T.corner[4 + f];
+            if (nq == NN) { Sx = sm.T.n[0][q]; Cx = sm.T.n[1][q]; }
+            else sincospif(fmaf(V.hx, zq, V.x0), &Sx, &Cx);
           }
         }
-        const float nv = part ? fmaf(s, q, ql) : 0.0f;
-        const float delta = block_max<NT>(part ? fabsf(nv - c2) : 0.0f, s_red);
-        c2 = nv;
-        if (delta <= tol) { conv = feasible; break; }
-        __syncthreads();
+        const float hn = f < 2 ? X.hx : X.hy;            // velocity in reference units times this = u.n
+        const float sg = (f == 0 || f == 2) ? -1.0f : 1.0f;
+        const float Wq = (f < 2 ? X.hy : X.hx) * rule[2 * NMAX + q];
+        float uo = 0.0f, ui = 0.0f, q1 = 0.0f, q2 = 0.0f;
+        for (int s = 0; s < S; ++s) {
+          const float cs = c_ds_c[P.rk][s];
+          float ur, vr;
+          vel_at(V, xr, yr, Sx, Cx, Sy, Cy, 0.0f, 0.0f, sm.T.ct[__float2int_rn(4.0f * cs)], ur, vr);
+          const float un = sg * (f < 2 ? ur : vr) * hn;
+          const float bw = c_ds_b[P.rk][s] * Wq * un;
+          if (un > (float)TIE) {
+            uo += bw;
+            float fdx = 0.0f, fdy = 0.0f;
+            if (cs != 0.0f) rk_disp(V, P.rk, xr, yr, Sx, Cx, Sy, Cy, fdx, fdy, -cs * X.dt, cs, -cs, sm.T.ct);
+            float bx[NN], by[NN];
+            basis_at<NN>(s_xi, s_lam, xr, fdx, bx);
+            basis_at<NN>(s_xi, s_lam, yr, fdy, by);
+            float val = 0.0f;
+#pragma unroll
+            for (int mm = 0; mm < NN; ++mm) val = fmaf(by[mm], row_dot<NN>(sm.psi + mm * NP, bx), val);
+            val += fmaf(gx, (xr - 0.5f) + fdx, gy * ((yr - 0.5f) + fdy));   // phi - r0 = (L - r0) + psi
+            q1 += bw * val;
+            q2 += bw * val * val;
+          } else if (un < -(float)TIE) {
+            ui += bw;
+          }
+        }
+        sm.fp[f][q][0] = uo;
+        sm.fp[f][q][1] = ui;
+        sm.fp[f][q][2] = q1;
+        sm.fp[f][q][3] = q2;
       }
-      if (conv) cur = c2 * usc;               // else keep the linear-constraint solution
-      ok = conv;
+      g.sync();
+      if (t < 4) {
+        const int f = t;
+        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int q = 0; q < sm.cum[f + 1] - sm.cum[f]; ++q)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) a[c] += sm.fp[f][q][c];
+        // the face's outflow flux of phi as a float-float value: r0 U_out + sum bw (phi - r0), plus
+        // the inflow of the ghost value through a domain face
+        ff Gf = ff_add(two_prod(r0, a[0]), ff{a[2], 0.0f});
+        if (nb_index(P, ex, ey, f) < 0) Gf = ff_add(Gf, two_prod((float)P.ghost, a[1]));
+        float* F = W.faces + E.g * 24 + 6 * f;
+        F[0] = Gf.hi;
+        F[1] = Gf.lo;
+        F[2] = a[0];
+        F[3] = a[1];
+        F[4] = a[2];
+        F[5] = a[3];
+      }
     }
   }
-  if (part) {
-    const double v = lref(ref, gx, gy, X.xid[i], X.xid[j]) + (double)cur;   // L + psi, split into hi + lo
-    const float s = (float)v;
-    out[E.base + tid] = s;
-    out[X.plane + E.base + tid] = (float)(v - (double)s);
-    if (!isfinite(s)) atomicOr(status, SL_ST_NONFINITE);
+  if (t == 0 && X0.counts) {
+    atomicAdd(X0.counts + SL_CNT_SOLVE_ITERS, c_it);
+    if (c_floor) atomicAdd(X0.counts + SL_CNT_SOLVE_FLOOR, c_floor);
+    if (c_nc) atomicAdd(X0.counts + SL_CNT_SOLVE_NOCONV, c_nc);
   }
-  if (!ok && tid == 0) atomicOr(status, SL_ST_PICARD_NOCONV);
+  if (bits) atomicOr(status, bits);
 }
 
+// ------------------------------------------------------------------ phase 2
+template <int NN>
+struct Smem2 {
+  static constexpr int ND = Shape<NN>::ND, G = Shape<NN>::G;
+  static constexpr int MMAX = 4 * NN + 1;
+  float a[ND];
+  float r[MMAX], ca[MMAX];
+  float red[4 * G];
+  float scal[8];
+};
+
+template <int NN>
+__global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
+    k_p2(StepParams P0, const __grid_constant__ Mixed2DExtra X0, Map2D M, int64_t count, const float* __restrict__ in,
+         Work2M W, float* __restrict__ out, unsigned* status) {
+  using S = Shape<NN>;
+  constexpr int ND = S::ND, G = S::G, GT = S::GT, EPC = S::EPC;
+  __shared__ float s_xi[NN], s_w[NN], s_l0[NN], s_l1[NN];
+  __shared__ Smem2<NN> sm_all[EPC];
+  if (threadIdx.x < NN) {
+    s_xi[threadIdx.x] = X0.xi[threadIdx.x];
+    s_w[threadIdx.x] = X0.w[threadIdx.x];
+    s_l0[threadIdx.x] = X0.l0[threadIdx.x];
+    s_l1[threadIdx.x] = X0.l1[threadIdx.x];
+  }
+  __syncthreads();
+  Grp<G> g;
+  g.slot = threadIdx.x / GT;
+  g.t = threadIdx.x % GT;
+  g.lane = threadIdx.x & 31;
+  g.w = g.t >> 5;
+  Smem2<NN>& sm = sm_all[g.slot];
+  g.red = sm.red;
+  g.rb = 0;
+  const int t = g.t;
+  const int p0 = t, p1 = t + GT;
+  const bool v0 = p0 < ND, v1 = p1 < ND;
+  const int i0 = p0 % NN, j0 = (p0 / NN) % NN, i1 = p1 % NN, j1 = (p1 / NN) % NN;
+  const float w20 = v0 ? s_w[i0] * s_w[j0] : 0.0f, w21 = v1 ? s_w[i1] * s_w[j1] : 0.0f;
+  unsigned long long c_el = 0, c_eapp = 0, c_pit = 0, c_pnc = 0;
+  unsigned bits = 0;
+  const int64_t ngroups = (int64_t)gridDim.x * EPC;
+  for (int64_t k = (int64_t)blockIdx.x * EPC + g.slot; k < count; k += ngroups) {
+    g.sync();
+    StepParams P = P0;
+    const Elem E = elem_at<NN>(P, M, k);
+    Mixed2DExtra X = X0;
+    batch_extra(P, M, X);
+    const int ex = E.ex, ey = E.ey;
+    const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
+    const VelElem V = make_vel(P, X, x0, y0);
+    const float* el = W.elem + E.g * 8;
+    const float r0 = el[0], gx = el[1], gy = el[2];
+    const float ph0 = v0 ? W.psihat[E.base + p0] : 0.0f;
+    const float ph1 = v1 ? W.psihat[E.base + p1] : 0.0f;
+    const bool bnd = (P.cons & SL_C_BOUNDARY) != 0;
+    const bool mass = (P.cons & SL_C_MASS) != 0, energy = (P.cons & SL_C_ENERGY) != 0;
+    const int nb_rows = bnd ? 4 * NN : 0;
+    if (bnd && t < 4 * NN) {
+      const int f = t / NN, q = t % NN;
+      const int nb = nb_index(P, ex, ey, f);
+      const float own = W.traces[E.g * M.tstride + t];
+      // neighbour's value at this element's face point relative to this element's L: the difference
+      // of the two references (float-float, of the size of psi when both fit the same data) plus the
+      // neighbour's trace of its own psihat
+      const float aq = s_xi[q] - 0.5f;
+      const float fa = f == 0 ? -0.5f : f == 1 ? 0.5f : aq, fb = f == 2 ? -0.5f : f == 3 ? 0.5f : aq;
+      const ff lown = lref(r0, gx, gy, fa, fb);
+      float other;
+      if (nb >= 0) {
+        const int64_t gn = E.gb + nb;
+        const int nn = order_of<NN>(M, gn);
+        const float* tr = W.traces + gn * M.tstride + (f ^ 1) * nn;
+        const float* en = W.elem + gn * 8;
+        const ff lnb = lref(en[0], en[1], en[2], f == 0 ? 0.5f : f == 1 ? -0.5f : fa, f == 2 ? 0.5f : f == 3 ? -0.5f : fb);
+        const float dl = __fadd_rn(__fsub_rn(lnb.hi, lown.hi), __fsub_rn(lnb.lo, lown.lo));
+        other = dl + (nn == NN ? tr[q] : interp_rule(X.rules, nn, tr, s_xi[q]));
+      } else {
+        other = __fsub_rn(__fsub_rn((float)P.ghost, lown.hi), lown.lo);
+      }
+      const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : s_xi[q];
+      const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : s_xi[q];
+      // one velocity evaluation per face point at t^{n+1}: sinpi/cospi directly
+      VelElem Vd = V;
+      Vd.direct = true;
+      const float ct = V.kind == SL_VEL_SWIRL ? cospif(X.tT + X.dtT) : 1.0f;
+      float ur, vr;
+      vel_at(Vd, xr, yr, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, ct, ur, vr);
+      const float un = (f == 0 || f == 2 ? -1.0f : 1.0f) * (f < 2 ? ur * X.hx : vr * X.hy);
+      float val;
+      if (un > (float)TIE) val = own;
+      else if (un < -(float)TIE) val = other;
+      else val = nb < 0 ? own : 0.5f * (own + other);
+      sm.r[t] = val - own;
+    }
+    // net outflow of mass (increments), of the squared increments and of the velocity, lanes 0-3 of
+    // the first warp one face each, summed in face order; the float-float mass target
+    if ((mass || energy) && t < 32) {
+      float cu = 0.0f, cm = 0.0f, cd = 0.0f;
+      ff net = {0.0f, 0.0f};
+      if (t < 4) {
+        const int f = t;
+        const float* F = W.faces + E.g * 24 + 6 * f;
+        const int nb = nb_index(P, ex, ey, f);
+        cu = F[2] + F[3];
+        net = ff{F[0], F[1]};
+        if (nb >= 0) {
+          const float* Gn = W.faces + (E.gb + nb) * 24 + 6 * (f ^ 1);
+          const float dref = W.elem[(E.gb + nb) * 8] - r0;
+          // inflow part: u.n (dref + psi_nb) with the neighbour's u.n = -ours
+          cm = F[4] + (dref * F[3] - Gn[4]);
+          cd = F[5] + (dref * dref * F[3] - 2.0f * dref * Gn[4] - Gn[5]);
+          net = ff_add(net, ff_neg(ff{Gn[0], Gn[1]}));
+        } else {
+          const float gg = (float)P.ghost - r0;
+          cm = F[4] + gg * F[3];
+          cd = F[5] + gg * gg * F[3];
+        }
+      }
+      float su = 0.0f, smm = 0.0f, sd = 0.0f;
+      ff sn = {0.0f, 0.0f};
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        su += __shfl_sync(0xffffffffu, cu, f);
+        smm += __shfl_sync(0xffffffffu, cm, f);
+        sd += __shfl_sync(0xffffffffu, cd, f);
+        sn = ff_add(sn, ff{__shfl_sync(0xffffffffu, net.hi, f), __shfl_sync(0xffffffffu, net.lo, f)});
+      }
+      if (t == 0) {
+        // M^{n+1} = M^n - dt / (hx hy) (net outflow), in float-float
+        const ff ln = ff_mul(sn, ff{X.lam_hi, X.lam_lo});
+        const ff target = ff_add(ff{el[5], el[6]}, ff_neg(ln));
+        sm.scal[0] = smm;
+        sm.scal[1] = sd;
+        sm.scal[2] = su;
+        sm.scal[3] = target.hi;
+        sm.scal[4] = target.lo;
+      }
+    }
+    g.sync();
+    const float netm = sm.scal[0], netd2 = sm.scal[1];
+    const ff target = {sm.scal[3], sm.scal[4]};
+    const float lam = X.dt_area;                  // dt / (hx hy)
+    const float m1 = el[3];
+    if (mass) {
+      const float mh = g.sum(fmaf(w20, ph0, w21 * ph1));
+      // target (increments): sum w psi^n - lam (net increment outflow + ref * closed-surface u.n);
+      // ref * (closed-surface integral of u.n) is dropped: every 2D velocity here is divergence free
+      // and the face quadrature integrates it to rounding (the refinement below meets the float-float
+      // target whatever this residual leaves)
+      if (t == 0) sm.r[nb_rows] = (m1 - lam * netm) - mh;
+    }
+    g.sync();
+    const int m = P.m;
+    float phL0 = ph0, phL1 = ph1;
+    for (int kk = 0; kk < m; ++kk) {
+      const float rk_ = sm.r[kk];
+      if (v0) phL0 = fmaf(X.Cp[(size_t)kk * ND + p0], rk_, phL0);
+      if (v1) phL1 = fmaf(X.Cp[(size_t)kk * ND + p1], rk_, phL1);
+    }
+    float cur0 = phL0, cur1 = phL1;
+    bool ok = true;
+    if (energy) {
+      // energy mismatch from increments (mass enforced): sum w (psiL - psi)(psiL + psi) + lam net(delta^2);
+      // without the mass row, add 2 ref times the mass residual (closed-surface u.n taken as zero)
+      float psin0 = 0.0f, psin1 = 0.0f;
+      if (v0) {
+        const ff L = lref(r0, gx, gy, s_xi[i0] - 0.5f, s_xi[j0] - 0.5f);
+        psin0 = __fadd_rn(__fsub_rn(in[E.base + p0], L.hi), __fsub_rn(in[X.plane + E.base + p0], L.lo));
+      }
+      if (v1) {
+        const ff L = lref(r0, gx, gy, s_xi[i1] - 0.5f, s_xi[j1] - 0.5f);
+        psin1 = __fadd_rn(__fsub_rn(in[E.base + p1], L.hi), __fsub_rn(in[X.plane + E.base + p1], L.lo));
+      }
+      const float dp0 = phL0 - psin0, dp1 = phL1 - psin1;
+      const float2 evml = g.sum2(fmaf(w20 * dp0, phL0 + (phL0 - dp0), w21 * dp1 * (phL1 + (phL1 - dp1))),
+                                 fmaf(w20, phL0, w21 * phL1));
+      const float ev = evml.x, ml = evml.y;
+      float gamma;
+      if (mass) gamma = ev + lam * netd2;
+      else gamma = fmaf(2.0f * r0, (ml - m1) + lam * netm, ev + lam * netd2);
+      const float escale = g.sum(fmaf(w20 * (r0 + cur0), r0 + cur0, w21 * (r0 + cur1) * (r0 + cur1)));
+      const float smax = g.max(fmaxf(fmaxf(fabsf(phL0), fabsf(phL1)), fabsf(r0)));
+      if (smax >= 1e-30f && fabsf(gamma) > (float)ENERGY_SKIP_RTOL_MIXED * escale) {
+        ++c_eapp;
+        int exn;
+        frexpf(smax, &exn);
+        const float sc = ldexpf(1.0f, -exn), usc = ldexpf(1.0f, exn);
+        const float rf = r0 * sc, gm = gamma * sc * sc;
+        const float ql0 = phL0 * sc, ql1 = phL1 * sc;
+        float c20 = ql0, c21 = ql1;
+        const float tol = 2.4e-7f + 1e-30f;         // scaled units: values are of order one
+        bool conv = false, feasible = true;
+        int it = 0;
+        for (; it < P.picard_cap; ++it) {
+          const float a0 = w20 * (mass ? c20 : rf + c20), a1 = w21 * (mass ? c21 : rf + c21);
+          if (v0) sm.a[p0] = a0;
+          if (v1) sm.a[p1] = a1;
+          g.sync();
+          if (bnd && t < 4 * NN) {
+            const int f = t / NN, qq = t % NN;
+            const float* Lb = (f == 1 || f == 3) ? s_l1 : s_l0;
+            float acc = 0.0f;
+            for (int kk = 0; kk < NN; ++kk) acc = fmaf(f < 2 ? sm.a[qq * NN + kk] : sm.a[kk * NN + qq], Lb[kk], acc);
+            sm.ca[t] = acc;
+          }
+          if (mass) {
+            const float cmm = g.sum(fmaf(w20, a0, w21 * a1));
+            if (t == 0) sm.ca[nb_rows] = cmm;
+          }
+          g.sync();
+          float q0 = a0, q1 = a1;
+          for (int kk = 0; kk < m; ++kk) {
+            const float ck = sm.ca[kk];
+            if (v0) q0 = fmaf(-X.Cp[(size_t)kk * ND + p0], ck, q0);
+            if (v1) q1 = fmaf(-X.Cp[(size_t)kk * ND + p1], ck, q1);
+          }
+          if (!v0) q0 = 0.0f;
+          if (!v1) q1 = 0.0f;
+          const float2 ab = g.sum2(fmaf(w20 * ql0, q0, w21 * ql1 * q1), fmaf(w20 * q0, q0, w21 * q1 * q1));
+          float alpha = ab.x;
+          if (!mass) alpha = fmaf(rf, g.sum(fmaf(w20, q0, w21 * q1)), alpha);
+          const float beta = ab.y;
+          float s;
+          if (beta <= 0.0f) { s = 0.0f; feasible = gm <= 0.0f; }
+          else {
+            const float disc = alpha * alpha - beta * gm;
+            if (disc < 0.0f) { s = -alpha / beta; feasible = false; }
+            else {
+              const float root = sqrtf(disc);
+              const float den = alpha + (alpha >= 0.0f ? root : -root);
+              s = den == 0.0f ? 0.0f : -gm / den;
+              feasible = true;
+            }
+          }
+          const float nv0 = v0 ? fmaf(s, q0, ql0) : 0.0f, nv1 = v1 ? fmaf(s, q1, ql1) : 0.0f;
+          const float delta = g.max(fmaxf(fabsf(nv0 - c20), fabsf(nv1 - c21)));
+          c20 = nv0;
+          c21 = nv1;
+          if (delta <= tol) { conv = feasible; break; }
+        }
+        c_pit += (unsigned long long)(it < P.picard_cap ? it + 1 : P.picard_cap);
+        if (conv) {                                 // else keep the linear-constraint solution
+          cur0 = c20 * usc;
+          cur1 = c21 * usc;
+        }
+        ok = conv;
+      }
+    }
+    // write-back v = L + psi as a float-float sum; with the mass row, one refinement step moves the
+    // float-float miss of the element mass along the pseudo-inverse column of the mass row (lo word)
+    ff vv0 = {0.0f, 0.0f}, vv1 = {0.0f, 0.0f};
+    if (v0) {
+      const ff L = lref(r0, gx, gy, s_xi[i0] - 0.5f, s_xi[j0] - 0.5f);
+      const ff s = two_sum(L.hi, cur0);
+      vv0 = fast_two_sum(s.hi, __fadd_rn(s.lo, L.lo));
+    }
+    if (v1) {
+      const ff L = lref(r0, gx, gy, s_xi[i1] - 0.5f, s_xi[j1] - 0.5f);
+      const ff s = two_sum(L.hi, cur1);
+      vv1 = fast_two_sum(s.hi, __fadd_rn(s.lo, L.lo));
+    }
+    if (mass) {
+      ff mv = {0.0f, 0.0f};
+      if (v0) mv = ff_mul(vv0, ff{X.w2h[p0], X.w2l[p0]});
+      if (v1) mv = ff_add(mv, ff_mul(vv1, ff{X.w2h[p1], X.w2l[p1]}));
+      mv = g.ffsum(mv);
+      const float miss = ff_to_f(ff_add(target, ff_neg(mv)));
+      const float* cmcol = X.Cp + (size_t)nb_rows * ND;
+      if (v0) vv0 = fast_two_sum(vv0.hi, fmaf(miss, cmcol[p0], vv0.lo));
+      if (v1) vv1 = fast_two_sum(vv1.hi, fmaf(miss, cmcol[p1], vv1.lo));
+    }
+    if (v0) {
+      out[E.base + p0] = vv0.hi;
+      out[X.plane + E.base + p0] = vv0.lo;
+      if (!isfinite(vv0.hi)) bits |= SL_ST_NONFINITE;
+    }
+    if (v1) {
+      out[E.base + p1] = vv1.hi;
+      out[X.plane + E.base + p1] = vv1.lo;
+      if (!isfinite(vv1.hi)) bits |= SL_ST_NONFINITE;
+    }
+    ++c_el;
+    if (!ok) {
+      bits |= SL_ST_PICARD_NOCONV;
+      ++c_pnc;
+    }
+  }
+  if (t == 0 && X0.counts) {
+    atomicAdd(X0.counts + SL_CNT_ELEMS, c_el);
+    if (c_eapp) atomicAdd(X0.counts + SL_CNT_ENERGY_APPLIED, c_eapp);
+    if (c_pit) atomicAdd(X0.counts + SL_CNT_PICARD_ITERS, c_pit);
+    if (c_pnc) atomicAdd(X0.counts + SL_CNT_PICARD_NOCONV, c_pnc);
+  }
+  if (bits) atomicOr(status, bits);
+}
+
+// persistent grid: the resident CTAs of the whole GPU, or one CTA per EPC elements if fewer
 template <int NN>
 void launch_n(int phase, const StepParams& p, const Mixed2DExtra& x, const Map2D& m, int64_t count, const float* in,
               float* out, const Work2M& w, unsigned* st, cudaStream_t s) {
   if (count <= 0) return;
-  if (phase == 1) k_p1<NN><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, x, m, in, w, st);
-  else k_p2<NN><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, x, m, in, w, out, st);
+  using S = Shape<NN>;
+  const int fill = phase == 1 ? persistent_grid((const void*)k_p1<NN>, S::NT, 0)
+                              : persistent_grid((const void*)k_p2<NN>, S::NT, 0);
+  const int64_t want = (count + S::EPC - 1) / S::EPC;
+  const unsigned grid = (unsigned)(want < fill ? want : fill);
+  if (phase == 1) k_p1<NN><<<grid, S::NT, 0, s>>>(p, x, m, count, in, w, st);
+  else k_p2<NN><<<grid, S::NT, 0, s>>>(p, x, m, count, in, w, out, st);
 }
 
 }  // namespace k2m

@@ -139,6 +139,16 @@ void build_ntab(sl_ntab& t, int n, int basis, int dim, bool mixed2d, TableBufs& 
     t.f_off[2] = B.fput(t.b.w);
     t.f_off[3] = B.fput(t.b.l0);
     t.f_off[4] = B.fput(t.b.l1);
+    // w_i w_j formed in double, as float-float (the element mass of the mixed path's refinement)
+    std::vector<double> w2h((size_t)n * n), w2l((size_t)n * n);
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const double v = t.b.w[i] * t.b.w[j];
+        w2h[(size_t)j * n + i] = (double)(float)v;
+        w2l[(size_t)j * n + i] = v - (double)(float)v;
+      }
+    t.f_off[5] = B.fput(w2h);
+    t.f_off[6] = B.fput(w2l);
     // the float pseudo-inverse is stored row of C first ([k][node]), so that the threads of an
     // element (one per node) read consecutive floats
     for (int mask = 0; mask < 4; ++mask) {
@@ -170,6 +180,25 @@ void build_rules(int basis, TableBufs& B, size_t& off, size_t& foff) {
 
 namespace sl {
 void set_global_error(const std::string& msg) { g_init_err = msg; }
+
+int persistent_grid(const void* kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  const auto key = std::make_tuple(dev, kernel, threads, smem);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaGetLastError();
+  const int grid = std::max(1, per_sm) * std::max(1, sms);
+  cache.emplace(key, grid);
+  return grid;
+}
 }  // namespace sl
 
 namespace {
@@ -188,7 +217,7 @@ void alias_ntab(sl_ctx* c) {
   c->off_lam = T.off_lam;
   c->off_l0 = T.off_l0;
   c->off_l1 = T.off_l1;
-  for (int k = 0; k < 5; ++k) c->f_off[k] = T.f_off[k];
+  for (int k = 0; k < 7; ++k) c->f_off[k] = T.f_off[k];
   for (int k = 0; k < 4; ++k) c->f_cp[k] = T.f_cp[k];
 }
 
@@ -199,6 +228,7 @@ sl_status alloc_upload(sl_ctx* c, const TableBufs& B, size_t work_bytes) {
       (work_bytes && cudaMalloc(&c->d_work, work_bytes) != cudaSuccess) ||
       (!B.ftab.empty() && cudaMalloc(&c->d_ftab, B.ftab.size() * sizeof(float)) != cudaSuccess) ||
       cudaMalloc(&c->d_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&c->d_counts, SL_NCOUNTERS * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&c->d_partial, c->red_blocks * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_result, sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -208,7 +238,8 @@ sl_status alloc_upload(sl_ctx* c, const TableBufs& B, size_t work_bytes) {
   if (cudaMemcpy(c->d_tables, B.host.data(), B.host.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
       (!B.ftab.empty() &&
        cudaMemcpy(c->d_ftab, B.ftab.data(), B.ftab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) ||
-      cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+      cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->d_counts, 0, SL_NCOUNTERS * sizeof(unsigned long long)) != cudaSuccess) {
     std::string msg = cudaGetErrorString(cudaGetLastError());
     sl_free(c);
     return fail(nullptr, SL_ECUDA, "table upload failed: " + msg);
@@ -263,7 +294,7 @@ sl_status finish_mapped(sl_ctx* c, const std::vector<uint16_t>& prob = {}) {
   }
   const size_t work_bytes = c->precision == SL_FP64
                                 ? (size_t)(c->nvals + nel * (4 * NMAX + 8)) * sizeof(double)
-                                : (size_t)(c->nvals + nel * (4 * NMAX + 16 + 8)) * sizeof(float);
+                                : (size_t)(c->nvals + nel * (4 * NMAX + WORK2M_FACE + WORK2M_ELEM)) * sizeof(float);
   sl_status st = alloc_upload(c, B, work_bytes);
   if (st != SL_OK) return st;
   const bool batch = !prob.empty();
@@ -359,6 +390,7 @@ void sl_free(sl_ctx* c) {
   if (!c) return;
   cudaFree(c->d_tables);
   cudaFree(c->d_status);
+  cudaFree(c->d_counts);
   cudaFree(c->d_partial);
   cudaFree(c->d_result);
   cudaFree(c->d_io);
@@ -523,19 +555,41 @@ void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, d
         Work2D w{W, W + c->nvals, W + c->nvals + nel * ts};
         launch_step2d_f64(phase, n, P, tb, map, count, (const double*)in, (double*)out, w, c->d_status, c->stream);
       } else {
-        Mixed2DExtra X{F + N.f_off[0], F + N.f_off[1], F + N.f_off[2], F + N.f_off[3], F + N.f_off[4],
-                       F + N.f_cp[lin], F + c->f_rules, T + N.off_xi,
-                       (opt->constraints & SL_C_ENERGY) ? 0 : 1, plane_stride(c->nvals),
-                       (float)hx, (float)hy, (float)(1.0 / hx), (float)(1.0 / hy),
-                       (float)vel->p[0], (float)vel->p[1], (float)vel->p[0], (float)vel->p[1], (float)vel->p[2],
-                       0.0f, 0.0f, (float)dt, (float)(dt / (hx * hy)), 0.0};
+        Mixed2DExtra X{};
+        X.xi = F + N.f_off[0];
+        X.lam = F + N.f_off[1];
+        X.w = F + N.f_off[2];
+        X.l0 = F + N.f_off[3];
+        X.l1 = F + N.f_off[4];
+        X.w2h = F + N.f_off[5];
+        X.w2l = F + N.f_off[6];
+        X.Cp = F + N.f_cp[lin];
+        X.rules = F + c->f_rules;
+        X.counts = c->d_counts;
+        X.linref = (opt->constraints & SL_C_ENERGY) ? 0 : 1;
+        X.plane = plane_stride(c->nvals);
+        X.span = (float)(0.5 / (N.b.xi[n - 1] - N.b.xi[0]));
+        X.hx = (float)hx;
+        X.hy = (float)hy;
+        X.ihx = (float)(1.0 / hx);
+        X.ihy = (float)(1.0 / hy);
+        X.a = (float)vel->p[0];
+        X.b = (float)vel->p[1];
+        X.om = (float)vel->p[0];
+        X.cx = (float)vel->p[1];
+        X.cy = (float)vel->p[2];
+        X.dt = (float)dt;
+        const double lam = dt / (hx * hy);
+        X.dt_area = (float)lam;
+        X.lam_hi = (float)lam;
+        X.lam_lo = (float)(lam - (double)X.lam_hi);
         if (vel->kind == SL_VEL_SWIRL) {
           X.tT = (float)(t / vel->p[0]);
           X.dtT = (float)(dt / vel->p[0]);
           X.Tper = vel->p[0];
         }
         float* W = (float*)c->d_work;
-        Work2M w{W, W + c->nvals, W + c->nvals + nel * ts, W + c->nvals + nel * (ts + 16)};
+        Work2M w{W, W + c->nvals, W + c->nvals + nel * ts, W + c->nvals + nel * (ts + WORK2M_FACE)};
         launch_step2d_mixed(phase, n, P, X, map, count, (const float*)in, (float*)out, w, c->d_status, c->stream);
       }
     }
@@ -882,6 +936,17 @@ sl_status sl_sync(sl_ctx* c, uint32_t* bits) {
   SL_CUDA(c, cudaMemset(c->d_status, 0, sizeof(unsigned)));
   if (bits) *bits = h;
   return h ? SL_EDEVICE : SL_OK;
+}
+
+sl_status sl_counters(sl_ctx* c, uint64_t* counts) {
+  if (!c) return SL_EINVAL;
+  if (!counts) return fail(c, SL_EINVAL, "null argument");
+  unsigned long long h[SL_NCOUNTERS] = {};
+  SL_CUDA(c, cudaStreamSynchronize(c->stream));
+  SL_CUDA(c, cudaMemcpy(h, c->d_counts, sizeof(h), cudaMemcpyDeviceToHost));
+  SL_CUDA(c, cudaMemset(c->d_counts, 0, sizeof(h)));
+  for (int k = 0; k < SL_NCOUNTERS; ++k) counts[k] = (uint64_t)h[k];
+  return SL_OK;
 }
 
 sl_status sl_max_dt(const sl_ctx* c, const sl_velocity* vel, int rule, double* dt) {

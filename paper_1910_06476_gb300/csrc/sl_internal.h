@@ -131,25 +131,30 @@ struct Mixed2DExtra {
   const float* l1;
   const float* Cp;                       // [m][n^2] pseudo-inverse of the active rows (hard fit)
   const float* rules;                    // [NMAX + 1][3][NMAX] xi, lam, w of every node count
-  const double* xid;                     // the nodes again, in double (element reference values)
+  const float* w2h;                      // [n^2] w_i w_j (formed in double) as float-float: hi
+  const float* w2l;                      //       and lo words
+  unsigned long long* counts;            // the context's work counters (SL_CNT_*), or null
   int linref;                            // 1: linear element reference (no energy row), 0: constant
   int64_t plane;                         // float offset of the lo plane
+  float span;                            // 1 / (2 (xi_{n-1} - xi_0)): corner differences to slopes
   float hx, hy, ihx, ihy;
   float a, b, om, cx, cy;                // velocity parameters (constant / rotation)
   float tT, dtT;                         // t / T and dt / T (swirl)
   float dt, dt_area;                     // dt and dt / (hx hy)
+  float lam_hi, lam_lo;                  // dt / (hx hy) as float-float
   double Tper;                           // swirl period T (per-problem t / T in a batch), else 0
 };
 struct Work2M {                          // mixed workspace between the two phases
   float* psihat;                         // same layout as the state (one plane)
   float* traces;                         // [nel][tstride]
-  float* faces;                          // [nel][4][4]  U_out, U_in, Psi, Psi2 per face
-  float* elem;                           // [nel][8]     r0, gx, gy, sum w psi, sum w psi^2, unused
+  float* faces;                          // [nel][4][6]  G_hi, G_lo (outflow flux of phi), U_out, U_in, P1, P2
+  float* elem;                           // [nel][8]     r0, gx, gy, sum w psi, sum w psi^2, M^n hi, lo, unused
 };
 void launch_step2d_mixed(int phase, int n, const StepParams& p, const Mixed2DExtra& x, const Map2D& m,
                          int64_t count, const float* in, float* out, const Work2M& w, unsigned* status,
                          cudaStream_t s);
-inline int64_t work2m_floats(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 16 + 8); }
+inline int64_t work2m_floats(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 24 + 8); }
+constexpr int WORK2M_FACE = 24, WORK2M_ELEM = 8;   // floats per element of the face and element records
 
 // Parameters of the 2D shared-operator kernel (uniform mesh, constant velocity).  Operators that
 // every thread applies with the same entry live here (the kernel reads them from the parameter
@@ -196,6 +201,10 @@ bool build_mixed1d(const sl_ctx* c, const FitOps& fit, double a, double dt, unsi
                    Mixed1DParams& P, std::string& err);
 void launch_step1d_mixed(const Mixed1DParams& p, const float* in, float* out, unsigned* status, cudaStream_t s);
 void launch_pack(int64_t nvals, int64_t plane, const double* src, float* dst, cudaStream_t s);
+// Grid of a persistent kernel: its resident CTAs per SM on the current device (occupancy calculator,
+// after raising the kernel's dynamic shared-memory limit to smem) times the SM count; cached per
+// (device, kernel, threads, smem) under a lock, so host threads on several devices may launch at once.
+int persistent_grid(const void* kernel, int threads, size_t smem);
 void launch_unpack(int64_t nvals, int64_t plane, const float* src, double* dst, cudaStream_t s);
 
 // float offset of the lo plane of a double-float state of nvals nodes: 256-byte aligned
@@ -223,7 +232,7 @@ struct sl_ntab {
   sl::FitOps fit[4][2];                  // [linear-row mask][soft]
   size_t off_xi = 0, off_w = 0, off_lam = 0, off_l0 = 0, off_l1 = 0;   // doubles
   size_t table_off[4][2][3] = {};        // Cpinv, S, SCt per mask / mode (doubles)
-  size_t f_off[5] = {};                  // xi, lam, w, l0, l1 (floats, mixed 2D)
+  size_t f_off[7] = {};                  // xi, lam, w, l0, l1, w2 hi, w2 lo (floats, mixed 2D)
   size_t f_cp[4] = {};                   // float pseudo-inverse per linear-row mask
 };
 
@@ -242,6 +251,7 @@ struct sl_ctx {
   size_t off_xi = 0, off_w = 0, off_lam = 0, off_l0 = 0, off_l1 = 0;
   size_t off_rules = 0;                  // [NMAX + 1][3][NMAX] xi, lam, w of every node count
   unsigned* d_status = nullptr;
+  unsigned long long* d_counts = nullptr;   // work counters (SL_CNT_*)
   double* d_partial = nullptr;           // reduction workspace
   double* d_result = nullptr;
   int red_blocks = 0;
@@ -282,7 +292,7 @@ struct sl_ctx {
   float* d_m2c = nullptr;
   size_t m2c_cap = 0;
   sl::Mixed2DConstParams m2c{};
-  size_t f_off[5] = {};                  // xi, lam, w, l0, l1
+  size_t f_off[7] = {};                  // xi, lam, w, l0, l1, w2 hi, w2 lo
   size_t f_cp[4] = {};                   // float pseudo-inverse per linear-row mask
   // cached shared operator of the mixed 1D path, keyed on (a, dt, constraints, rk, fit)
   bool mix_valid = false;

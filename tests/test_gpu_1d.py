@@ -242,4 +242,5 @@ def test_energy_row_in_skip_band_fp64(sl):
     assert band.size > 100, band.size
     assert all(infos[k]["converged"] for k in range(K)) and bits == 0
     compare(setup, got, ref)
-    compare(setup, got[band], ref[band])
+    relb = np.sqrt(np.sum((got[band] - ref[band]) ** 2) / np.sum(ref[band] ** 2))
+    assert relb <= TOL_REL, relb

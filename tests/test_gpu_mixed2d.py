@@ -168,3 +168,52 @@ def test_mixed2d_swirl_1024_sampled(sl):
     g = np.stack([got[ey, ex] for ex, ey in elems])
     r = np.stack([ref[ey, ex] for ex, ey in elems])
     assert rel(g, r) <= TOL
+
+
+@pytest.mark.parametrize("kind,p,bc", [(2, (5.0,), 1), (0, (1.0, 0.0), 0), (1, (2 * np.pi, 0.5, 0.5), 0)])
+def test_mixed2d_general_mass_to_roundoff(sl, kind, p, bc):
+    """The general mixed kernel conserves global mass to round-off: element masses and face
+    outflow fluxes are float-float values, each face flux enters both elements as the same
+    number, and one refinement step brings every element's mass to its target (Sec. 4.3, eq.
+    remap_mass).  Closed domains: the swirl (zero normal velocity on the walls), axis-aligned
+    constant flow and solid-body rotation on periodic squares (the rotation's flux through a
+    periodic face leaves and re-enters); 300 steps, boundary + mass, relative drift <= 1e-12."""
+    K, n = 24, 8
+    ctx = sl.Context(2, K, K, (0.0, 1.0, 0.0, 1.0), n, 0, sl.MIXED, (bc,) * 4, 0.0)
+    gv = sl.velocity(kind, *p)
+    dt = ctx.max_dt(gv, sl.RULE_PAPER)
+    x, y = ctx.node_coords()
+    phi = 1.0 + sl_inputs.cosine_bell_2d(x, y) + 0.2 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    a = ctx.pack(torch.tensor(phi.ravel(), device="cuda"))
+    b = ctx.new_state()
+    m0 = ctx.mass(a)
+    opts = sl.options(sl.C_BOUNDARY | sl.C_MASS, 4)
+    for s in range(300):
+        ctx.step(a, b, gv, s * dt, dt, opts)
+        a, b = b, a
+    assert ctx.sync() & ~sl.ST_SOLVE_FLOOR == 0
+    assert abs(ctx.mass(a) - m0) <= 1e-12 * abs(m0), (ctx.mass(a) - m0) / m0
+
+
+def test_mixed2d_counters(sl):
+    """sl_counters of the general mixed kernel: one element update per element and step, at least
+    one collocation iteration each, and the energy iteration counted only where it ran."""
+    prob = sl_inputs.config5_swirl(n=8, k=32)
+    ctx = sl.Context(2, 32, 32, prob.box, 8, 0, sl.MIXED, prob.bc, prob.ghost)
+    gv = sl.velocity(sl.VEL_SWIRL, 5.0)
+    dt = ctx.max_dt(gv, sl.RULE_PAPER)
+    x, y = ctx.node_coords()
+    a = ctx.pack(torch.tensor(prob.phi0(x, y).ravel(), device="cuda"))
+    b = ctx.new_state()
+    ctx.counters()
+    for s in range(3):
+        ctx.step(a, b, gv, s * dt, dt, sl.options(prob.constraints, 4))
+        a, b = b, a
+    bits = ctx.sync()
+    c = ctx.counters()
+    assert c["elems"] == 3 * 32 * 32, c
+    assert 3 * 32 * 32 <= c["solve_iters"] <= 3 * 32 * 32 * 40, c
+    assert c["picard_iters"] >= c["energy_applied"] > 0, c
+    assert (c["picard_noconv"] > 0) == bool(bits & sl.ST_PICARD_NOCONV), (c, bits)
+    assert (c["solve_floor"] > 0) == bool(bits & sl.ST_SOLVE_FLOOR), (c, bits)
+    assert ctx.counters() == dict.fromkeys(c, 0)

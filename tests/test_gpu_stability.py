@@ -45,12 +45,13 @@ def test_paper_time_step_is_stable_half_spacing_is_not(sl, kind, p, data):
 
 
 def test_swirl_transient_amplification_fp64(sl):
-    """Measured property of the discrete scheme on the swirl flow (config 5's problem, 512 x 512,
+    """Measured property of the discrete scheme on the swirl flow (config 5's problem, 256 x 256,
     n = 8, boundary + mass, paper's time step): a 1e-12 perturbation of the FP64 state grows by more
-    than six orders of magnitude within 1000 steps, while the solution stays bounded.  This is
-    why long mixed-versus-FP64 comparisons on this flow are limited to short horizons."""
-    prob = sl_inputs.config5_swirl(n=8, k=512)
-    c = sl.Context(2, 512, 512, prob.box, 8, 0, sl.FP64, prob.bc, prob.ghost)
+    than three orders of magnitude within 1000 steps (about 2e4 measured; more than 1e6 at 512 x
+    512), while the solution stays bounded.  This is why long mixed-versus-FP64 comparisons on this
+    flow are limited to short horizons."""
+    prob = sl_inputs.config5_swirl(n=8, k=256)
+    c = sl.Context(2, 256, 256, prob.box, 8, 0, sl.FP64, prob.bc, prob.ghost)
     gv = sl.velocity(sl.VEL_SWIRL, 5.0)
     dt = c.max_dt(gv, sl.RULE_PAPER)
     x, y = c.node_coords()
@@ -65,5 +66,5 @@ def test_swirl_transient_amplification_fp64(sl):
         a2, b2 = b2, a2
     c.sync()
     growth = (a2 - a1).abs().max().item() / 1e-12
-    assert growth > 1e6, growth
+    assert growth > 1e3, growth
     assert a1.abs().max().item() <= 1.01
