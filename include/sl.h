@@ -266,7 +266,9 @@ sl_status sl_integral_noalloc(const double* phi, int64_t nelem, int nper, int di
  *                          iteration of Sec. 4.3 ran;
  *   SL_CNT_PICARD_ITERS    iterations of that energy iteration;
  *   SL_CNT_PICARD_NOCONV   elements where it did not converge and the linear-constraint fit was
- *                          kept (SL_ST_PICARD_NOCONV).
+ *                          kept (SL_ST_PICARD_NOCONV);
+ *   SL_CNT_FEET            outflow face points (per distinct RK stage time after t^n) whose
+ *                          backward characteristic foot was traced for the mass/energy flux.
  * counts (host) receives SL_NCOUNTERS values; the call synchronises the context's stream and resets
  * the counters.  Other paths leave them unchanged. */
 enum {
@@ -277,9 +279,23 @@ enum {
   SL_CNT_ENERGY_APPLIED = 4,
   SL_CNT_PICARD_ITERS = 5,
   SL_CNT_PICARD_NOCONV = 6,
+  SL_CNT_FEET = 7,
   SL_NCOUNTERS = 8
 };
 sl_status sl_counters(sl_ctx* ctx, uint64_t* counts);
+
+/* Device time of the step's kernels, measured with CUDA events on the context's stream (the
+ * stream the kernels are launched on).  sl_timing(ctx, 1) starts a session: every following sl_step,
+ * sl_batch_step or sl_run_host step records an event before its first kernel, one between the two
+ * phases of the two-dimensional general path (phase 1: advection, collocation solve, traces and face
+ * outflow; phase 2: interface values, targets, fit and write-back) and one after its last kernel;
+ * steps inside sl_run's captured graphs are not timed.  sl_timing(ctx, 0) ends the session and
+ * releases its events.  Both synchronise the stream.  sl_timing_read synchronises and returns, for
+ * the steps of the session so far, the summed milliseconds ms[0] of phase 1 (the whole kernel of a
+ * single-kernel path), ms[1] of phase 2 (0 there) and ms[2] of both, and *nsteps, the number of timed
+ * steps.  Timing adds three event records per step and nothing else to the work. */
+sl_status sl_timing(sl_ctx* ctx, int enable);
+sl_status sl_timing_read(sl_ctx* ctx, double* ms, int* nsteps);
 
 /* Last error message of the context (or of the last failed sl_init when ctx is null). */
 const char* sl_last_error(const sl_ctx* ctx);

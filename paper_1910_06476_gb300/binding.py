@@ -24,12 +24,12 @@ BV_INTERP, BV_BACKTRACK = 0, 1
 RULE_HALF_MIN_SPACING, RULE_PAPER = 0, 1
 ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV, ST_TIMEOUT, ST_SOLVE_FLOOR = 1, 2, 4, 8, 16
 COUNTERS = ("elems", "solve_iters", "solve_floor", "solve_noconv", "energy_applied", "picard_iters",
-            "picard_noconv", "reserved")
+            "picard_noconv", "feet")
 
 EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
            "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",
            "sl_integral_noalloc", "sl_batch_create", "sl_batch_step", "sl_batch_offset", "sl_counters",
-           "sl_last_error"]
+           "sl_timing", "sl_timing_read", "sl_last_error"]
 
 
 class SlMesh(C.Structure):
@@ -75,6 +75,8 @@ def load_library(path=LIB_PATH):
     lib.sl_energy.argtypes = [P, P, C.POINTER(C.c_double)]
     lib.sl_sync.argtypes = [P, C.POINTER(C.c_uint32)]
     lib.sl_counters.argtypes = [P, C.POINTER(C.c_uint64)]
+    lib.sl_timing.argtypes = [P, C.c_int]
+    lib.sl_timing_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.sl_max_dt.argtypes = [P, C.POINTER(SlVelocity), C.c_int, C.POINTER(C.c_double)]
     lib.sl_state_size.argtypes = [P]
     lib.sl_state_size.restype = C.c_int64
@@ -245,6 +247,17 @@ class Context:
         arr = (C.c_uint64 * len(COUNTERS))()
         self._check(self._lib.sl_counters(self._h, arr))
         return dict(zip(COUNTERS, (int(v) for v in arr)))
+
+    def timing(self, enable):
+        """Start (True) or end (False) a kernel-timing session (sl_timing)."""
+        self._check(self._lib.sl_timing(self._h, 1 if enable else 0))
+
+    def timing_read(self):
+        """(phase-1 ms, phase-2 ms, total ms, timed steps) of the session so far (sl_timing_read)."""
+        ms = (C.c_double * 3)()
+        k = C.c_int()
+        self._check(self._lib.sl_timing_read(self._h, ms, C.byref(k)))
+        return ms[0], ms[1], ms[2], k.value
 
     def max_dt(self, vel, rule=RULE_HALF_MIN_SPACING):
         out = C.c_double()

@@ -1,5 +1,5 @@
 // Dispatch of the 2D FP64 step kernels on the node count.
-#include "k_step2d_impl.cuh"
+#include "k_map2d.cuh"   // declarations only: the kernels are instantiated in k_step2d_{a..d}.cu
 
 namespace sl {
 namespace k2d {

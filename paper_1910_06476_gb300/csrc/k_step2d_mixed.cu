@@ -1,5 +1,5 @@
 // Dispatch of the 2D mixed-precision step kernels on the node count.
-#include "k_step2d_mixed_impl.cuh"
+#include "k_map2d.cuh"   // declarations only: the kernels are instantiated in k_step2d_mixed_{a..c}.cu
 
 namespace sl {
 namespace k2m {

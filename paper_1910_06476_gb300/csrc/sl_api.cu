@@ -408,6 +408,7 @@ void sl_free(sl_ctx* c) {
   if (c->run_ev[0]) cudaEventDestroy(c->run_ev[0]);
   if (c->run_ev[1]) cudaEventDestroy(c->run_ev[1]);
   if (c->run_stream) cudaStreamDestroy(c->run_stream);
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   delete c;
 }
 
@@ -513,6 +514,30 @@ sl_status check_dt(sl_ctx* c, const sl_mesh& M, const sl_velocity* vel, double t
   return SL_OK;
 }
 
+// Event k (0 start, 1 between the phases, 2 end) of the current timed step; steps captured into a
+// graph (sl_run) are not timed.
+void timing_mark(sl_ctx* c, int k) {
+  if (!c->timing || c->capturing) return;
+  if (k == 0) {
+    if (c->tused + 3 > c->tev.size()) {
+      for (int i = 0; i < 3; ++i) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          cudaGetLastError();
+          c->timing = false;
+          return;
+        }
+        c->tev.push_back(e);
+      }
+    }
+    c->tused += 3;
+    c->tdone.resize(c->tused / 3);
+    c->tdone.back() = 0;
+  }
+  cudaEventRecord(c->tev[c->tused - 3 + k], c->stream);
+  if (k == 2) c->tdone.back() = 1;
+}
+
 // the general 2D kernels: phase 1 of every node-count bucket, then phase 2 of every bucket
 void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, double dt, const sl_options* opt,
                     const void* in, void* out) {
@@ -533,7 +558,8 @@ void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, d
   const float* F = c->d_ftab;
   const sl_mesh& M = c->mesh;
   const double hx = (M.x1 - M.x0) / M.kx, hy = (M.y1 - M.y0) / M.ky;
-  for (int phase = 1; phase <= 2; ++phase)
+  for (int phase = 1; phase <= 2; ++phase) {
+    if (phase == 2) timing_mark(c, 1);
     for (int n = 2; n <= NMAX; ++n) {
       int64_t count;
       if (c->mapped) {
@@ -593,6 +619,7 @@ void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, d
         launch_step2d_mixed(phase, n, P, X, map, count, (const float*)in, (float*)out, w, c->d_status, c->stream);
       }
     }
+  }
 }
 
 // the mixed 2D constant-velocity path (one operator shared by every element)
@@ -660,6 +687,7 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
 
   const double* T = c->d_tables;
   const size_t* off = c->table_off[lin][opt->fit == SL_FIT_SOFT];
+  timing_mark(c, 0);
   if (M.dim == 1 && c->precision == SL_FP64) {
     Tables1D tb{T + c->off_xi, T + c->off_w, T + c->off_lam, T + c->off_l0, T + c->off_l1,
                 T + off[0], T + off[1], T + off[2]};
@@ -703,6 +731,11 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
     step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
   } else {
     return fail(c, SL_EUNSUPPORTED, "this dimension/precision combination is not built yet");
+  }
+  if (c->timing && !c->capturing) {
+    const bool two_phase = M.dim == 2 && !uses_m2c(c, vel, opt);
+    if (!two_phase) timing_mark(c, 1);
+    timing_mark(c, 2);
   }
   SL_CUDA(c, cudaGetLastError());
   return SL_OK;
@@ -806,7 +839,13 @@ sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, do
     }
     const cudaStream_t user = c->stream;
     c->stream = c->run_stream;
-    SL_CUDA(c, cudaStreamBeginCapture(c->run_stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    const cudaError_t cb = cudaStreamBeginCapture(c->run_stream, cudaStreamCaptureModeThreadLocal);
+    if (cb != cudaSuccess) {
+      c->stream = user;
+      c->capturing = false;
+      return fail(c, SL_ECUDA, std::string("capture: ") + cudaGetErrorString(cb));
+    }
     void* a = phi_a;
     void* b = phi_b;
     for (int s = 0; s < nsteps && st == SL_OK; ++s) {
@@ -817,6 +856,7 @@ sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, do
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(c->run_stream, &graph);
     c->stream = user;
+    c->capturing = false;
     c->geo_override = nullptr;
     if (st == SL_OK && ce != cudaSuccess) st = fail(c, SL_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
     if (st == SL_OK && cudaGraphInstantiate(&c->run_exec, graph, 0) != cudaSuccess) {
@@ -936,6 +976,44 @@ sl_status sl_sync(sl_ctx* c, uint32_t* bits) {
   SL_CUDA(c, cudaMemset(c->d_status, 0, sizeof(unsigned)));
   if (bits) *bits = h;
   return h ? SL_EDEVICE : SL_OK;
+}
+
+sl_status sl_timing(sl_ctx* c, int enable) {
+  if (!c) return SL_EINVAL;
+  SL_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!enable) {
+    for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+    c->tev.clear();
+  }
+  c->tused = 0;
+  c->tdone.clear();
+  c->timing = enable != 0;
+  return SL_OK;
+}
+
+sl_status sl_timing_read(sl_ctx* c, double* ms, int* nsteps) {
+  if (!c) return SL_EINVAL;
+  if (!ms || !nsteps) return fail(c, SL_EINVAL, "null argument");
+  SL_CUDA(c, cudaStreamSynchronize(c->stream));
+  double a = 0.0, b = 0.0;
+  int done = 0;
+  for (size_t k = 0; k + 3 <= c->tused; k += 3) {
+    float t01 = 0.0f, t12 = 0.0f;
+    // a step that failed after its start event has no end event: it is not counted
+    if (!c->tdone[k / 3] || cudaEventElapsedTime(&t01, c->tev[k], c->tev[k + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t12, c->tev[k + 1], c->tev[k + 2]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    a += t01;
+    b += t12;
+    ++done;
+  }
+  ms[0] = a;
+  ms[1] = b;
+  ms[2] = a + b;
+  *nsteps = done;
+  return SL_OK;
 }
 
 sl_status sl_counters(sl_ctx* c, uint64_t* counts) {

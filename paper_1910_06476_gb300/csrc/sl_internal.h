@@ -300,5 +300,11 @@ struct sl_ctx {
   unsigned mix_cons = 0;
   int mix_rk = 0, mix_fit = 0;
   sl::Mixed1DParams mix{};
+  // kernel timing (sl_timing): three events per timed step (start, between the two phases, end)
+  bool timing = false;
+  bool capturing = false;                // sl_run is recording its graph
+  std::vector<cudaEvent_t> tev;          // 3 per step, reused across timing sessions
+  size_t tused = 0;                      // events of the current session
+  std::vector<char> tdone;               // per timed step: its end event was recorded
   std::string err;
 };

@@ -217,3 +217,51 @@ def test_mixed2d_counters(sl):
     assert (c["picard_noconv"] > 0) == bool(bits & sl.ST_PICARD_NOCONV), (c, bits)
     assert (c["solve_floor"] > 0) == bool(bits & sl.ST_SOLVE_FLOOR), (c, bits)
     assert ctx.counters() == dict.fromkeys(c, 0)
+
+
+def test_mixed2d_solve_status_bits_and_counters(sl):
+    """Coarse meshes (2 x 2, 3 x 3 elements) at a large step deform each element so much that the
+    collocation iteration preconditioned by the mean displacement stalls or diverges.  Every such
+    element is reported: accepted between the float floor and 1e-4 (SL_ST_SOLVE_FLOOR) or not
+    accepted (SL_ST_SOLVE_NOCONV), each bit set exactly when its counter is non-zero, and both
+    outcomes occur in this set of cases (nothing is accepted silently above the floor)."""
+    seen = 0
+    for K, n, frac in [(2, 4, 0.2), (2, 6, 0.1), (3, 8, 0.1), (3, 4, 0.3), (2, 8, 0.5)]:
+        ctx = sl.Context(2, K, K, (0.0, 1.0, 0.0, 1.0), n, 0, sl.MIXED, (1,) * 4, 0.0)
+        gv = sl.velocity(sl.VEL_SWIRL, 5.0)
+        x, y = ctx.node_coords()
+        phi = sl_inputs.cosine_bell_2d(x, y) + 0.3 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        a = ctx.pack(torch.tensor(phi.ravel(), device="cuda"))
+        b = ctx.new_state()
+        ctx.counters()
+        ctx.step(a, b, gv, 0.0, frac / K, sl.options(3, 4))
+        bits = ctx.sync()
+        c = ctx.counters()
+        assert bool(bits & sl.ST_SOLVE_FLOOR) == (c["solve_floor"] > 0), (K, n, frac, bits, c)
+        assert bool(bits & sl.ST_SOLVE_NOCONV) == (c["solve_noconv"] > 0), (K, n, frac, bits, c)
+        assert c["elems"] == K * K
+        seen |= bits
+    assert seen & sl.ST_SOLVE_FLOOR and seen & sl.ST_SOLVE_NOCONV, seen
+
+
+def test_kernel_timing_session(sl):
+    """sl_timing: CUDA events around the two phases of the general kernels, summed per session;
+    steps inside sl_run's graphs are not timed; the sum of the phases is the step."""
+    prob = sl_inputs.config5_swirl(n=8, k=64)
+    ctx = sl.Context(2, 64, 64, prob.box, 8, 0, sl.MIXED, prob.bc, prob.ghost)
+    gv = sl.velocity(sl.VEL_SWIRL, 5.0)
+    dt = ctx.max_dt(gv, sl.RULE_PAPER)
+    x, y = ctx.node_coords()
+    a = ctx.pack(torch.tensor(prob.phi0(x, y).ravel(), device="cuda"))
+    b = ctx.new_state()
+    opts = sl.options(prob.constraints, 4)
+    ctx.timing(True)
+    for s in range(4):
+        ctx.step(a, b, gv, s * dt, dt, opts)
+        a, b = b, a
+    ctx.run(a, b, gv, 4 * dt, dt, 2, opts)
+    p1, p2, tot, k = ctx.timing_read()
+    assert k == 4 and p1 > 0 and p2 > 0 and abs(tot - (p1 + p2)) < 1e-9
+    ctx.timing(False)
+    ctx.step(a, b, gv, 0.0, dt, opts)
+    assert ctx.timing_read()[3] == 0
