@@ -43,16 +43,6 @@
 namespace sl {
 namespace k2m {
 
-static __constant__ int c_rk_s[5] = {0, 1, 2, 3, 4};
-static __constant__ float c_rk_a[5][4][4] = {
-    {},
-    {{0}},
-    {{0, 0}, {1.0f, 0}},
-    {{0, 0, 0}, {0.5f, 0, 0}, {-1.0f, 2.0f, 0}},
-    {{0, 0, 0, 0}, {0.5f, 0, 0, 0}, {0, 0.5f, 0, 0}, {0, 0, 1.0f, 0}}};
-static __constant__ float c_rk_b[5][4] = {
-    {}, {1.0f}, {0.5f, 0.5f}, {1.0f / 6, 2.0f / 3, 1.0f / 6}, {1.0f / 6, 1.0f / 3, 1.0f / 3, 1.0f / 6}};
-static __constant__ float c_rk_c[5][4] = {{}, {0.0f}, {0.0f, 1.0f}, {0.0f, 0.5f, 1.0f}, {0.0f, 0.5f, 0.5f, 1.0f}};
 // distinct stage times of the face-flux quadrature and their summed weights (RK4's two c = 1/2
 // stages see the same face velocity and the same foot)
 static __constant__ int c_ds_n[5] = {0, 1, 2, 3, 3};
@@ -287,37 +277,71 @@ __device__ __forceinline__ void vel_at(const VelElem& V, float bx, float by, flo
   }
 }
 
+// Butcher tableaux of the explicit RK schemes of orders 1-4 (forward Euler, Heun, Kutta's third
+// order, classical), as compile-time functions so that the coefficients become immediates
+template <int RK>
+struct Tab {
+  static constexpr int S = RK;
+  __device__ static constexpr float a(int s, int j) {
+    return RK == 2 ? (s == 1 && j == 0 ? 1.0f : 0.0f)
+         : RK == 3 ? (s == 1 && j == 0 ? 0.5f : s == 2 && j == 0 ? -1.0f : s == 2 && j == 1 ? 2.0f : 0.0f)
+         : RK == 4 ? ((s == 1 && j == 0) || (s == 2 && j == 1) ? 0.5f : s == 3 && j == 2 ? 1.0f : 0.0f)
+                   : 0.0f;
+  }
+  __device__ static constexpr float b(int s) {
+    return RK == 1 ? 1.0f
+         : RK == 2 ? 0.5f
+         : RK == 3 ? (s == 1 ? 2.0f / 3.0f : 1.0f / 6.0f)
+                   : (s == 0 || s == 3 ? 1.0f / 6.0f : 1.0f / 3.0f);
+  }
+  __device__ static constexpr float c(int s) {
+    return RK == 2 ? (s == 1 ? 1.0f : 0.0f)
+         : RK == 3 ? (s == 1 ? 0.5f : s == 2 ? 1.0f : 0.0f)
+         : RK == 4 ? (s == 1 || s == 2 ? 0.5f : s == 3 ? 1.0f : 0.0f)
+                   : 0.0f;
+  }
+};
+
 // One RK step of the displacement (dx, dy) of a point over a time step h (negative: backward), the
 // stage time of stage s being the step fraction f0 + c_s fstep (one of 0, 1/4, 1/2, 3/4, 1, whose
 // cos(pi tau / T) are ctab[0..4]).  The displacement is integrated by itself (not the position), so
 // that its float rounding is relative to the displacement.
-__device__ __forceinline__ void rk_disp(const VelElem& V, int rk, float bx, float by, float Sx, float Cx, float Sy,
-                                        float Cy, float& dx, float& dy, float h, float f0, float fstep,
-                                        const float* ctab) {
-  const int S = c_rk_s[rk];
-  float kx[4], ky[4];
+template <int RK>
+__device__ __forceinline__ void rk_disp_t(const VelElem& V, float bx, float by, float Sx, float Cx, float Sy, float Cy,
+                                          float& dx, float& dy, float h, float f0, float fstep, const float* ctab) {
+  using T = Tab<RK>;
+  float kx[T::S], ky[T::S];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (s < S) {
-      float xs = dx, ys = dy;
+  for (int s = 0; s < T::S; ++s) {
+    float xs = dx, ys = dy;
 #pragma unroll
-      for (int j = 0; j < s; ++j) {
-        xs = fmaf(h * c_rk_a[rk][s][j], kx[j], xs);
-        ys = fmaf(h * c_rk_a[rk][s][j], ky[j], ys);
+    for (int j = 0; j < s; ++j)
+      if (T::a(s, j) != 0.0f) {
+        xs = fmaf(h * T::a(s, j), kx[j], xs);
+        ys = fmaf(h * T::a(s, j), ky[j], ys);
       }
-      const int ci = __float2int_rn(4.0f * fmaf(c_rk_c[rk][s], fstep, f0));
-      vel_at(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ctab[ci], kx[s], ky[s]);
-    }
+    const int ci = __float2int_rn(4.0f * fmaf(T::c(s), fstep, f0));
+    vel_at(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ctab[ci], kx[s], ky[s]);
   }
   float sx = 0.0f, sy = 0.0f;
 #pragma unroll
-  for (int s = 0; s < 4; ++s)
-    if (s < S) {
-      sx = fmaf(c_rk_b[rk][s], kx[s], sx);
-      sy = fmaf(c_rk_b[rk][s], ky[s], sy);
-    }
+  for (int s = 0; s < T::S; ++s) {
+    sx = fmaf(T::b(s), kx[s], sx);
+    sy = fmaf(T::b(s), ky[s], sy);
+  }
   dx = fmaf(h, sx, dx);
   dy = fmaf(h, sy, dy);
+}
+
+__device__ __forceinline__ void rk_disp(const VelElem& V, int rk, float bx, float by, float Sx, float Cx, float Sy,
+                                        float Cy, float& dx, float& dy, float h, float f0, float fstep,
+                                        const float* ctab) {
+  switch (rk) {
+    case 4: rk_disp_t<4>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
+    case 3: rk_disp_t<3>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
+    case 2: rk_disp_t<2>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
+    default: rk_disp_t<1>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab);
+  }
 }
 
 // vel_at at two points at once (paired float operations; the direct evaluation per component)
@@ -356,35 +380,54 @@ __device__ __forceinline__ void vel_at2(const VelElem& V, float2 bx, float2 by, 
   }
 }
 
-// rk_disp for two points at once
-__device__ __forceinline__ void rk_disp2(const VelElem& V, int rk, float2 bx, float2 by, float2 Sx, float2 Cx,
-                                         float2 Sy, float2 Cy, float2& dx, float2& dy, float h, float f0, float fstep,
-                                         const float* ctab) {
-  const int S = c_rk_s[rk];
-  float2 kx[4], ky[4];
+// rk_disp for two points at once (paired float operations)
+template <int RK>
+__device__ __forceinline__ void rk_disp2_t(const VelElem& V, float2 bx, float2 by, float2 Sx, float2 Cx, float2 Sy,
+                                           float2 Cy, float2& dx, float2& dy, float h, const float* ctab) {
+  using T = Tab<RK>;
+  float2 kx[T::S], ky[T::S];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (s < S) {
-      float2 xs = dx, ys = dy;
+  for (int s = 0; s < T::S; ++s) {
+    float2 xs = dx, ys = dy;
 #pragma unroll
-      for (int j = 0; j < s; ++j) {
-        const float2 hj = bc2(h * c_rk_a[rk][s][j]);
+    for (int j = 0; j < s; ++j)
+      if (T::a(s, j) != 0.0f) {
+        const float2 hj = bc2(h * T::a(s, j));
         xs = fma2(hj, kx[j], xs);
         ys = fma2(hj, ky[j], ys);
       }
-      const int ci = __float2int_rn(4.0f * fmaf(c_rk_c[rk][s], fstep, f0));
-      vel_at2(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ctab[ci], kx[s], ky[s]);
-    }
+    vel_at2(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ctab[__float2int_rn(4.0f * T::c(s))], kx[s], ky[s]);
   }
   float2 sx = bc2(0.0f), sy = bc2(0.0f);
 #pragma unroll
-  for (int s = 0; s < 4; ++s)
-    if (s < S) {
-      sx = fma2(bc2(c_rk_b[rk][s]), kx[s], sx);
-      sy = fma2(bc2(c_rk_b[rk][s]), ky[s], sy);
-    }
+  for (int s = 0; s < T::S; ++s) {
+    sx = fma2(bc2(T::b(s)), kx[s], sx);
+    sy = fma2(bc2(T::b(s)), ky[s], sy);
+  }
   dx = fma2(bc2(h), sx, dx);
   dy = fma2(bc2(h), sy, dy);
+}
+
+// forward step over the whole step h = dt from t^n
+__device__ __forceinline__ void rk_disp2(const VelElem& V, int rk, float2 bx, float2 by, float2 Sx, float2 Cx,
+                                         float2 Sy, float2 Cy, float2& dx, float2& dy, float h, const float* ctab) {
+  switch (rk) {
+    case 4: rk_disp2_t<4>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
+    case 3: rk_disp2_t<3>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
+    case 2: rk_disp2_t<2>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
+    default: rk_disp2_t<1>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab);
+  }
+}
+
+// velocity at a base point itself (no displacement): the tabulated sines and cosines directly
+__device__ __forceinline__ void vel_base(const VelElem& V, float bx, float by, float Sx, float Cx, float Sy, float Cy,
+                                         float ct, float& u, float& v) {
+  if (V.kind == SL_VEL_SWIRL && !V.direct) {
+    u = Sx * Sx * (2.0f * Sy * Cy) * ct * V.ihx;
+    v = -Sy * Sy * (2.0f * Sx * Cx) * ct * V.ihy;
+  } else {
+    vel_at(V, bx, by, Sx, Cx, Sy, Cy, 0.0f, 0.0f, ct, u, v);
+  }
 }
 
 // Lagrange basis at z = z0 + dz with the differences formed as (z0 - xi_k) + dz: when z0 is a
@@ -667,7 +710,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
     rk_disp2(V, P.rk, make_float2(s_xi[i0], s_xi[i1]), make_float2(s_xi[j0], s_xi[j1]),
              make_float2(sm.T.n[0][i0], sm.T.n[0][i1]), make_float2(sm.T.n[1][i0], sm.T.n[1][i1]),
              make_float2(sm.T.n[2][j0], sm.T.n[2][j1]), make_float2(sm.T.n[3][j0], sm.T.n[3][j1]), d2x, d2y, X.dt,
-             0.0f, 1.0f, sm.T.ct);
+             sm.T.ct);
     const float dx0 = v0 ? d2x.x : 0.0f, dy0 = v0 ? d2y.x : 0.0f, dx1 = v1 ? d2x.y : 0.0f, dy1 = v1 ? d2y.y : 0.0f;
     float2 Lx[NN], Ly[NN];
     basis_at2<NN>(s_xi, s_lam, s_xi[i0], s_xi[i1], dx0, dx1, Lx);
@@ -852,43 +895,50 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
         const float hn = f < 2 ? X.hx : X.hy;            // velocity in reference units times this = u.n
         const float sg = (f == 0 || f == 2) ? -1.0f : 1.0f;
         const float Wq = (f < 2 ? X.hy : X.hx) * (nq == NN ? s_w[q] : X.rules[(size_t)nq * 3 * NMAX + 2 * NMAX + q]);
+        // phi - r0 at the face point itself (stage time t^n): the trace of psi^n plus (L - r0)
+        float val0;
+        if (nq == NN) {
+          const float* Lb = (f == 1 || f == 3) ? s_l1 : s_l0;
+          float acc = 0.0f;
+#pragma unroll
+          for (int kk = 0; kk < NN; ++kk) acc = fmaf(f < 2 ? sm.psi[q * NP + kk] : sm.psi[kk * NP + q], Lb[kk], acc);
+          val0 = acc;
+        } else {
+          float bx[NN], by[NN];
+          basis_at<NN>(s_xi, s_lam, xr, 0.0f, bx);
+          basis_at<NN>(s_xi, s_lam, yr, 0.0f, by);
+          float acc = 0.0f;
+#pragma unroll
+          for (int mm = 0; mm < NN; ++mm) acc = fmaf(by[mm], row_dot<NN>(sm.psi + mm * NP, bx), acc);
+          val0 = acc;
+        }
+        val0 += fmaf(gx, xr - 0.5f, gy * (yr - 0.5f));
+        // per distinct stage time: the sign of u.n, the weight; later stage times that flow out
+        // are queued for their backward foot (their weight kept in fbo, 0 otherwise)
+        float uo = 0.0f, ui = 0.0f, q1 = 0.0f, q2 = 0.0f;
         for (int s = 0; s < S; ++s) {
           const float cs = c_ds_c[P.rk][s];
           float ur, vr;
-          vel_at(V, xr, yr, Sx, Cx, Sy, Cy, 0.0f, 0.0f, sm.T.ct[__float2int_rn(4.0f * cs)], ur, vr);
+          vel_base(V, xr, yr, Sx, Cx, Sy, Cy, sm.T.ct[__float2int_rn(4.0f * cs)], ur, vr);
           const float un = sg * (f < 2 ? ur : vr) * hn;
           const float bw = c_ds_b[P.rk][s] * Wq * un;
-          float bo = 0.0f, bi = 0.0f, val = 0.0f;
-          if (un > (float)TIE) {
-            bo = bw;
-            if (cs == 0.0f) {
-              // psi^n at the face point itself: a trace of the own polynomial
-              if (nq == NN) {
-                const float* Lb = (f == 1 || f == 3) ? s_l1 : s_l0;
-                float acc = 0.0f;
-#pragma unroll
-                for (int kk = 0; kk < NN; ++kk) acc = fmaf(f < 2 ? sm.psi[q * NP + kk] : sm.psi[kk * NP + q], Lb[kk], acc);
-                val = acc;
-              } else {
-                float bx[NN], by[NN];
-                basis_at<NN>(s_xi, s_lam, xr, 0.0f, bx);
-                basis_at<NN>(s_xi, s_lam, yr, 0.0f, by);
-                float acc = 0.0f;
-#pragma unroll
-                for (int mm = 0; mm < NN; ++mm) acc = fmaf(by[mm], row_dot<NN>(sm.psi + mm * NP, bx), acc);
-                val = acc;
-              }
-              val += fmaf(gx, xr - 0.5f, gy * (yr - 0.5f));   // phi - r0 = (L - r0) + psi
-            } else {
-              sm.u.fc.items[atomicAdd(&sm.nitems, 1)] = idx * 4 + s;
+          const bool out = un > (float)TIE;
+          if (out) uo += bw;
+          if (un < -(float)TIE) ui += bw;
+          if (cs == 0.0f) {
+            if (out) {
+              q1 = fmaf(bw, val0, q1);
+              q2 = fmaf(bw * val0, val0, q2);
             }
-          } else if (un < -(float)TIE) {
-            bi = bw;
+          } else {
+            sm.u.fc.fbo[f][q][s] = out ? bw : 0.0f;
+            if (out) sm.u.fc.items[atomicAdd(&sm.nitems, 1)] = idx * 4 + s;
           }
-          sm.u.fc.fbo[f][q][s] = bo;
-          sm.u.fc.fbi[f][q][s] = bi;
-          sm.u.fc.fv[f][q][s] = val;
         }
+        sm.u.fc.pt[f][q][0] = uo;
+        sm.u.fc.pt[f][q][1] = ui;
+        sm.u.fc.pt[f][q][2] = q1;
+        sm.u.fc.pt[f][q][3] = q2;
       }
       g.sync();
       const int nitems = sm.nitems;
@@ -912,23 +962,23 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
         sm.u.fc.fv[f][q][s] = val;
       }
       g.sync();
-      // per face point: the sums over the stage times (each point's own slots, in stage order)
-      for (int idx = t; idx < total; idx += GT) {
-        const int f = (idx >= sm.cum[1]) + (idx >= sm.cum[2]) + (idx >= sm.cum[3]);
-        const int q = idx - sm.cum[f];
-        float uo = 0.0f, ui = 0.0f, q1 = 0.0f, q2 = 0.0f;
-        for (int s = 0; s < S; ++s) {
-          const float bo = sm.u.fc.fbo[f][q][s], v = sm.u.fc.fv[f][q][s];
-          uo += bo;
-          ui += sm.u.fc.fbi[f][q][s];
-          q1 = fmaf(bo, v, q1);
-          q2 = fmaf(bo * v, v, q2);
+      // per face point: the outflow of the later stage times, added in stage order
+      if (S > 1)
+        for (int idx = t; idx < total; idx += GT) {
+          const int f = (idx >= sm.cum[1]) + (idx >= sm.cum[2]) + (idx >= sm.cum[3]);
+          const int q = idx - sm.cum[f];
+          float q1 = sm.u.fc.pt[f][q][2], q2 = sm.u.fc.pt[f][q][3];
+          for (int s = 1; s < S; ++s) {
+            const float bo = sm.u.fc.fbo[f][q][s];
+            if (bo != 0.0f) {
+              const float v = sm.u.fc.fv[f][q][s];
+              q1 = fmaf(bo, v, q1);
+              q2 = fmaf(bo * v, v, q2);
+            }
+          }
+          sm.u.fc.pt[f][q][2] = q1;
+          sm.u.fc.pt[f][q][3] = q2;
         }
-        sm.u.fc.pt[f][q][0] = uo;
-        sm.u.fc.pt[f][q][1] = ui;
-        sm.u.fc.pt[f][q][2] = q1;
-        sm.u.fc.pt[f][q][3] = q2;
-      }
       g.sync();
       // per face and quantity (16 threads): the sum over the face's points in point order
       if (t < 16) {
