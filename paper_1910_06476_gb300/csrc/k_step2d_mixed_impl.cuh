@@ -38,6 +38,8 @@
 // while h <= 1/4, so that |pi h d| <= pi / 4 where ten terms are exact to 1e-9; coarser meshes evaluate
 // sinpi and cospi directly).  cos(pi t / T) is taken once per element at the stage-time fractions 0,
 // 1/4, 1/2, 3/4, 1 of the step, which cover the RK schemes and their backward feet.
+#include <type_traits>
+
 #include "k_map2d.cuh"
 
 namespace sl {
@@ -88,6 +90,15 @@ __device__ __forceinline__ ff ff_mul(ff a, ff w) {
   return fast_two_sum(p.hi, fmaf(a.hi, w.lo, fmaf(a.lo, w.hi, p.lo)));
 }
 __device__ __forceinline__ float ff_to_f(ff a) { return __fadd_rn(a.hi, a.lo); }
+
+// asynchronous 4-byte global-to-shared copies (the next element's inputs are staged while the current
+// one is computed); a thread waits for its own copies, a group barrier then publishes them
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // element reference L at reference coordinates given as (a, b) = (xi - 1/2, eta - 1/2): the linear
 // part is rounded once, L = r0 + t exactly as a float-float value.  Every use runs this same
@@ -636,6 +647,7 @@ struct Smem1 {
   int cum[5];
   int nitems;
   Trig<NN> T;
+  float sth[2][ND], stl[2][ND];                // staged input state (hi, lo) of this and the next element
 };
 
 template <int NN>
@@ -669,8 +681,22 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
   unsigned long long c_it = 0, c_floor = 0, c_nc = 0, c_feet = 0;
   unsigned bits = 0;
   const int64_t ngroups = (int64_t)gridDim.x * EPC;
-  for (int64_t k = (int64_t)blockIdx.x * EPC + g.slot; k < count; k += ngroups) {
+  // asynchronous copies of element kk's input state into staging buffer b (one group per call)
+  auto stage = [&](int64_t kk, int b) {
+    if (kk < count) {
+      StepParams Pn = P0;
+      const Elem En = elem_at<NN>(Pn, M, kk);
+      if (v0) { cp_async4(&sm.sth[b][p0], in + En.base + p0); cp_async4(&sm.stl[b][p0], in + X0.plane + En.base + p0); }
+      if (v1) { cp_async4(&sm.sth[b][p1], in + En.base + p1); cp_async4(&sm.stl[b][p1], in + X0.plane + En.base + p1); }
+    }
+    cp_async_commit();
+  };
+  int64_t k = (int64_t)blockIdx.x * EPC + g.slot;
+  stage(k, 0);
+  for (int b = 0; k < count; k += ngroups, b ^= 1) {
     g.sync();                                    // the previous element's shared data is consumed
+    stage(k + ngroups, b ^ 1);
+    cp_async_wait1();
     StepParams P = P0;
     const Elem E = elem_at<NN>(P, M, k);
     Mixed2DExtra X = X0;
@@ -679,8 +705,11 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
     const float x0 = (float)(P.x0 + ex * P.hx), y0 = (float)(P.y0 + ey * P.hy);
     const VelElem V = make_vel(P, X, x0, y0);
     trig_setup<NN>(g, V, X, s_xi, sm.T);
+    g.sync();                                    // this element's staged state is visible
+    const float* sh = sm.sth[b];
+    const float* sl = sm.stl[b];
     // element reference: linear from the four corner values, or the first node value
-    const float c00 = in[E.base], c01 = in[E.base + NN - 1], c10 = in[E.base + (NN - 1) * NN], c11 = in[E.base + ND - 1];
+    const float c00 = sh[0], c01 = sh[NN - 1], c10 = sh[(NN - 1) * NN], c11 = sh[ND - 1];
     float r0 = c00, gx = 0.0f, gy = 0.0f;
     if (X.linref) {
       r0 = 0.25f * ((c00 + c01) + (c10 + c11));
@@ -691,14 +720,14 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
     float pn0 = 0.0f, pn1 = 0.0f;
     ff mn = {0.0f, 0.0f};
     if (v0) {
-      const float hi = in[E.base + p0], lo = in[X.plane + E.base + p0];
+      const float hi = sh[p0], lo = sl[p0];
       const ff L = lref(r0, gx, gy, s_xi[i0] - 0.5f, s_xi[j0] - 0.5f);
       pn0 = __fadd_rn(__fsub_rn(hi, L.hi), __fsub_rn(lo, L.lo));
       sm.psi[j0 * NP + i0] = pn0;
       mn = ff_mul(ff{hi, lo}, ff{X.w2h[p0], X.w2l[p0]});
     }
     if (v1) {
-      const float hi = in[E.base + p1], lo = in[X.plane + E.base + p1];
+      const float hi = sh[p1], lo = sl[p1];
       const ff L = lref(r0, gx, gy, s_xi[i1] - 0.5f, s_xi[j1] - 0.5f);
       pn1 = __fadd_rn(__fsub_rn(hi, L.hi), __fsub_rn(lo, L.lo));
       sm.psi[j1 * NP + i1] = pn1;
@@ -864,13 +893,22 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
       g.sync();
       const int S = c_ds_n[P.rk];
       const int total = sm.cum[4];
-      // geometry of face point idx: face, point, rule, reference coordinates, sines and cosines
-      auto face_point = [&](int idx, int& f, int& q, int& nq, float& xr, float& yr, float& Sx, float& Cx, float& Sy,
-                            float& Cy) {
-        f = (idx >= sm.cum[1]) + (idx >= sm.cum[2]) + (idx >= sm.cum[3]);
-        q = idx - sm.cum[f];
-        nq = sm.cum[f + 1] - sm.cum[f];
-        const float zq = nq == NN ? s_xi[q] : X.rules[(size_t)nq * 3 * NMAX + q];
+      // Geometry of face point idx: face, point, rule, reference coordinates, sines and cosines.
+      // CONF: every face takes the element's own rule (conforming neighbours), so that no lane
+      // carries the general rule's branches.
+      auto face_point = [&](auto conf, int idx, int& f, int& q, int& nq, float& xr, float& yr, float& Sx, float& Cx,
+                            float& Sy, float& Cy) {
+        constexpr bool CONF = decltype(conf)::value;
+        if (CONF) {
+          f = idx / NN;
+          q = idx % NN;
+          nq = NN;
+        } else {
+          f = (idx >= sm.cum[1]) + (idx >= sm.cum[2]) + (idx >= sm.cum[3]);
+          q = idx - sm.cum[f];
+          nq = sm.cum[f + 1] - sm.cum[f];
+        }
+        const float zq = (CONF || nq == NN) ? s_xi[q] : X.rules[(size_t)nq * 3 * NMAX + q];
         xr = f == 0 ? 0.0f : f == 1 ? 1.0f : zq;
         yr = f == 2 ? 0.0f : f == 3 ? 1.0f : zq;
         Sx = Cx = Sy = Cy = 0.0f;
@@ -878,26 +916,30 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
           if (f < 2) {
             Sx = sm.T.corner[f];
             Cx = sm.T.corner[4 + f];
-            if (nq == NN) { Sy = sm.T.n[2][q]; Cy = sm.T.n[3][q]; }
+            if (CONF || nq == NN) { Sy = sm.T.n[2][q]; Cy = sm.T.n[3][q]; }
             else sincospif(fmaf(V.hy, zq, V.y0), &Sy, &Cy);
           } else {
             Sy = sm.T.corner[f];
             Cy = sm.T.corner[4 + f];
-            if (nq == NN) { Sx = sm.T.n[0][q]; Cx = sm.T.n[1][q]; }
+            if (CONF || nq == NN) { Sx = sm.T.n[0][q]; Cx = sm.T.n[1][q]; }
             else sincospif(fmaf(V.hx, zq, V.x0), &Sx, &Cx);
           }
         }
       };
+      const bool conforming = total == 4 * NN;
+      auto pass1 = [&](auto conf) {
+      constexpr bool CONF = decltype(conf)::value;
       for (int idx = t; idx < total; idx += GT) {
         int f, q, nq;
         float xr, yr, Sx, Cx, Sy, Cy;
-        face_point(idx, f, q, nq, xr, yr, Sx, Cx, Sy, Cy);
+        face_point(conf, idx, f, q, nq, xr, yr, Sx, Cx, Sy, Cy);
         const float hn = f < 2 ? X.hx : X.hy;            // velocity in reference units times this = u.n
         const float sg = (f == 0 || f == 2) ? -1.0f : 1.0f;
-        const float Wq = (f < 2 ? X.hy : X.hx) * (nq == NN ? s_w[q] : X.rules[(size_t)nq * 3 * NMAX + 2 * NMAX + q]);
+        const float Wq = (f < 2 ? X.hy : X.hx) *
+                         ((CONF || nq == NN) ? s_w[q] : X.rules[(size_t)nq * 3 * NMAX + 2 * NMAX + q]);
         // phi - r0 at the face point itself (stage time t^n): the trace of psi^n plus (L - r0)
         float val0;
-        if (nq == NN) {
+        if (CONF || nq == NN) {
           const float* Lb = (f == 1 || f == 3) ? s_l1 : s_l0;
           float acc = 0.0f;
 #pragma unroll
@@ -932,7 +974,16 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
             }
           } else {
             sm.u.fc.fbo[f][q][s] = out ? bw : 0.0f;
-            if (out) sm.u.fc.items[atomicAdd(&sm.nitems, 1)] = idx * 4 + s;
+            // queue the pair: one shared atomic per warp (lane order within the warp)
+            const unsigned act = __activemask();
+            const unsigned want = __ballot_sync(act, out);
+            if (want) {
+              const int leader = __ffs(act) - 1;
+              int base = 0;
+              if (g.lane == leader) base = atomicAdd(&sm.nitems, __popc(want));
+              base = __shfl_sync(act, base, leader);
+              if (out) sm.u.fc.items[base + __popc(want & ((1u << g.lane) - 1u))] = idx * 4 + s;
+            }
           }
         }
         sm.u.fc.pt[f][q][0] = uo;
@@ -940,6 +991,9 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
         sm.u.fc.pt[f][q][2] = q1;
         sm.u.fc.pt[f][q][3] = q2;
       }
+      };
+      if (conforming) pass1(std::true_type{});
+      else pass1(std::false_type{});
       g.sync();
       const int nitems = sm.nitems;
       c_feet += (unsigned long long)nitems;
@@ -948,7 +1002,8 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
         const int idx = code >> 2, s = code & 3;
         int f, q, nq;
         float xr, yr, Sx, Cx, Sy, Cy;
-        face_point(idx, f, q, nq, xr, yr, Sx, Cx, Sy, Cy);
+        if (conforming) face_point(std::true_type{}, idx, f, q, nq, xr, yr, Sx, Cx, Sy, Cy);
+        else face_point(std::false_type{}, idx, f, q, nq, xr, yr, Sx, Cx, Sy, Cy);
         const float cs = c_ds_c[P.rk][s];
         float fdx = 0.0f, fdy = 0.0f;
         rk_disp(V, P.rk, xr, yr, Sx, Cx, Sy, Cy, fdx, fdy, -cs * X.dt, cs, -cs, sm.T.ct);

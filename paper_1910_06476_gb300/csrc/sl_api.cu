@@ -190,11 +190,21 @@ int persistent_grid(const void* kernel, int threads, size_t smem) {
   std::lock_guard<std::mutex> lock(mu);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the dynamic allowance is raised whenever a kernel takes any: static plus dynamic shared memory
+  // above 48 KB needs it, whatever the split
+  // A failed call leaves its error as the last error; it is cleared here, which loses nothing:
+  // every kernel launch is checked as soon as it is enqueued, so no earlier error is pending.
+  if (smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    cudaGetLastError();
   int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaGetLastError();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) {
+    per_sm = 1;
+    cudaGetLastError();
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    sms = 152;
+    cudaGetLastError();
+  }
   const int grid = std::max(1, per_sm) * std::max(1, sms);
   cache.emplace(key, grid);
   return grid;
@@ -538,9 +548,10 @@ void timing_mark(sl_ctx* c, int k) {
   if (k == 2) c->tdone.back() = 1;
 }
 
-// the general 2D kernels: phase 1 of every node-count bucket, then phase 2 of every bucket
-void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, double dt, const sl_options* opt,
-                    const void* in, void* out) {
+// the general 2D kernels: phase 1 of every node-count bucket, then phase 2 of every bucket; each
+// launch is checked as it is enqueued
+sl_status step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, double dt, const sl_options* opt,
+                         const void* in, void* out) {
   const unsigned lin = opt->constraints & 3u;
   const int soft = opt->fit == SL_FIT_SOFT ? 1 : 0;
   const int64_t nel = c->nel;
@@ -580,6 +591,7 @@ void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, d
         double* W = c->d_work;
         Work2D w{W, W + c->nvals, W + c->nvals + nel * ts};
         launch_step2d_f64(phase, n, P, tb, map, count, (const double*)in, (double*)out, w, c->d_status, c->stream);
+        SL_CUDA(c, cudaGetLastError());
       } else {
         Mixed2DExtra X{};
         X.xi = F + N.f_off[0];
@@ -617,9 +629,11 @@ void step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double t, d
         float* W = (float*)c->d_work;
         Work2M w{W, W + c->nvals, W + c->nvals + nel * ts, W + c->nvals + nel * (ts + WORK2M_FACE)};
         launch_step2d_mixed(phase, n, P, X, map, count, (const float*)in, (float*)out, w, c->d_status, c->stream);
+        SL_CUDA(c, cudaGetLastError());
       }
     }
   }
+  return SL_OK;
 }
 
 // the mixed 2D constant-velocity path (one operator shared by every element)
@@ -717,7 +731,8 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
   } else if (M.dim == 2 && c->precision == SL_FP64) {
     if (opt->bvalue != SL_BV_INTERP)
       return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
-    step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
+    const sl_status st = step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
+    if (st != SL_OK) return st;
   } else if (uses_m2c(c, vel, opt)) {
     // uniform mesh, constant velocity: one operator shared by all elements
     sl_status st = ensure_m2c(c, vel, dt, opt);
@@ -728,7 +743,8 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
     if (opt->bvalue != SL_BV_INTERP)
       return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
     if (opt->fit != SL_FIT_HARD) return fail(c, SL_EUNSUPPORTED, "the 2D mixed path uses the hard fit");
-    step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
+    const sl_status st = step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
+    if (st != SL_OK) return st;
   } else {
     return fail(c, SL_EUNSUPPORTED, "this dimension/precision combination is not built yet");
   }
