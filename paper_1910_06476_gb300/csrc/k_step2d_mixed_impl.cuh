@@ -317,7 +317,20 @@ struct Tab {
 // stage time of stage s being the step fraction f0 + c_s fstep (one of 0, 1/4, 1/2, 3/4, 1, whose
 // cos(pi tau / T) are ctab[0..4]).  The displacement is integrated by itself (not the position), so
 // that its float rounding is relative to the displacement.
-template <int RK>
+// velocity of the swirl at a displaced point from the tabulated sines (angle addition)
+__device__ __forceinline__ void vel_swirl_tab(const VelElem& V, float Sx, float Cx, float Sy, float Cy, float dx,
+                                              float dy, float ct, float& u, float& v) {
+  float st, ctt;
+  small_sincos(V.pihx * dx, V.shortser, st, ctt);
+  const float sx = fmaf(Sx, ctt, Cx * st), cx = fmaf(Cx, ctt, -Sx * st);
+  small_sincos(V.pihy * dy, V.shortser, st, ctt);
+  const float sy = fmaf(Sy, ctt, Cy * st), cy = fmaf(Cy, ctt, -Sy * st);
+  u = sx * sx * (2.0f * sy * cy) * ct * V.ihx;
+  v = -sy * sy * (2.0f * sx * cx) * ct * V.ihy;
+}
+
+// TAB: the velocity is the swirl from the tabulated sines (chosen once per element)
+template <int RK, bool TAB>
 __device__ __forceinline__ void rk_disp_t(const VelElem& V, float bx, float by, float Sx, float Cx, float Sy, float Cy,
                                           float& dx, float& dy, float h, float f0, float fstep, const float* ctab) {
   using T = Tab<RK>;
@@ -332,7 +345,8 @@ __device__ __forceinline__ void rk_disp_t(const VelElem& V, float bx, float by, 
         ys = fmaf(h * T::a(s, j), ky[j], ys);
       }
     const int ci = __float2int_rn(4.0f * fmaf(T::c(s), fstep, f0));
-    vel_at(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ctab[ci], kx[s], ky[s]);
+    if (TAB) vel_swirl_tab(V, Sx, Cx, Sy, Cy, xs, ys, ctab[ci], kx[s], ky[s]);
+    else vel_at(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ctab[ci], kx[s], ky[s]);
   }
   float sx = 0.0f, sy = 0.0f;
 #pragma unroll
@@ -347,11 +361,15 @@ __device__ __forceinline__ void rk_disp_t(const VelElem& V, float bx, float by, 
 __device__ __forceinline__ void rk_disp(const VelElem& V, int rk, float bx, float by, float Sx, float Cx, float Sy,
                                         float Cy, float& dx, float& dy, float h, float f0, float fstep,
                                         const float* ctab) {
+  if (rk == 4 && V.kind == SL_VEL_SWIRL && !V.direct) {
+    rk_disp_t<4, true>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab);
+    return;
+  }
   switch (rk) {
-    case 4: rk_disp_t<4>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
-    case 3: rk_disp_t<3>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
-    case 2: rk_disp_t<2>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
-    default: rk_disp_t<1>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab);
+    case 4: rk_disp_t<4, false>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
+    case 3: rk_disp_t<3, false>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
+    case 2: rk_disp_t<2, false>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab); break;
+    default: rk_disp_t<1, false>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, f0, fstep, ctab);
   }
 }
 
@@ -392,7 +410,7 @@ __device__ __forceinline__ void vel_at2(const VelElem& V, float2 bx, float2 by, 
 }
 
 // rk_disp for two points at once (paired float operations)
-template <int RK>
+template <int RK, bool TAB>
 __device__ __forceinline__ void rk_disp2_t(const VelElem& V, float2 bx, float2 by, float2 Sx, float2 Cx, float2 Sy,
                                            float2 Cy, float2& dx, float2& dy, float h, const float* ctab) {
   using T = Tab<RK>;
@@ -407,7 +425,18 @@ __device__ __forceinline__ void rk_disp2_t(const VelElem& V, float2 bx, float2 b
         xs = fma2(hj, kx[j], xs);
         ys = fma2(hj, ky[j], ys);
       }
-    vel_at2(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ctab[__float2int_rn(4.0f * T::c(s))], kx[s], ky[s]);
+    const float ct = ctab[__float2int_rn(4.0f * T::c(s))];
+    if (TAB) {
+      float2 st, ctt;
+      small_sincos2(mul2(bc2(V.pihx), xs), V.shortser, st, ctt);
+      const float2 sx = fma2(Sx, ctt, mul2(Cx, st)), cx = fma2(Cx, ctt, mul2(neg2(Sx), st));
+      small_sincos2(mul2(bc2(V.pihy), ys), V.shortser, st, ctt);
+      const float2 sy = fma2(Sy, ctt, mul2(Cy, st)), cy = fma2(Cy, ctt, mul2(neg2(Sy), st));
+      kx[s] = mul2(mul2(sx, sx), mul2(mul2(sy, cy), bc2(2.0f * ct * V.ihx)));
+      ky[s] = mul2(mul2(sy, sy), mul2(mul2(sx, cx), bc2(-2.0f * ct * V.ihy)));
+    } else {
+      vel_at2(V, bx, by, Sx, Cx, Sy, Cy, xs, ys, ct, kx[s], ky[s]);
+    }
   }
   float2 sx = bc2(0.0f), sy = bc2(0.0f);
 #pragma unroll
@@ -422,11 +451,15 @@ __device__ __forceinline__ void rk_disp2_t(const VelElem& V, float2 bx, float2 b
 // forward step over the whole step h = dt from t^n
 __device__ __forceinline__ void rk_disp2(const VelElem& V, int rk, float2 bx, float2 by, float2 Sx, float2 Cx,
                                          float2 Sy, float2 Cy, float2& dx, float2& dy, float h, const float* ctab) {
+  if (rk == 4 && V.kind == SL_VEL_SWIRL && !V.direct) {
+    rk_disp2_t<4, true>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab);
+    return;
+  }
   switch (rk) {
-    case 4: rk_disp2_t<4>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
-    case 3: rk_disp2_t<3>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
-    case 2: rk_disp2_t<2>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
-    default: rk_disp2_t<1>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab);
+    case 4: rk_disp2_t<4, false>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
+    case 3: rk_disp2_t<3, false>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
+    case 2: rk_disp2_t<2, false>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab); break;
+    default: rk_disp2_t<1, false>(V, bx, by, Sx, Cx, Sy, Cy, dx, dy, h, ctab);
   }
 }
 
@@ -927,8 +960,11 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
         }
       };
       const bool conforming = total == 4 * NN;
-      auto pass1 = [&](auto conf) {
+      const bool tab = V.kind == SL_VEL_SWIRL && !V.direct;
+      // CONF: conforming faces; TAB: the swirl from the tabulated sines (both known per element)
+      auto pass1 = [&](auto conf, auto tabc) {
       constexpr bool CONF = decltype(conf)::value;
+      constexpr bool TAB = decltype(tabc)::value;
       for (int idx = t; idx < total; idx += GT) {
         int f, q, nq;
         float xr, yr, Sx, Cx, Sy, Cy;
@@ -961,7 +997,13 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
         for (int s = 0; s < S; ++s) {
           const float cs = c_ds_c[P.rk][s];
           float ur, vr;
-          vel_base(V, xr, yr, Sx, Cx, Sy, Cy, sm.T.ct[__float2int_rn(4.0f * cs)], ur, vr);
+          const float ct = sm.T.ct[__float2int_rn(4.0f * cs)];
+          if (TAB) {
+            ur = Sx * Sx * (2.0f * Sy * Cy) * ct * V.ihx;
+            vr = -Sy * Sy * (2.0f * Sx * Cx) * ct * V.ihy;
+          } else {
+            vel_at(V, xr, yr, Sx, Cx, Sy, Cy, 0.0f, 0.0f, ct, ur, vr);
+          }
           const float un = sg * (f < 2 ? ur : vr) * hn;
           const float bw = c_ds_b[P.rk][s] * Wq * un;
           const bool out = un > (float)TIE;
@@ -992,8 +1034,8 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
         sm.u.fc.pt[f][q][3] = q2;
       }
       };
-      if (conforming) pass1(std::true_type{});
-      else pass1(std::false_type{});
+      if (conforming && tab) pass1(std::true_type{}, std::true_type{});
+      else pass1(std::false_type{}, std::false_type{});
       g.sync();
       const int nitems = sm.nitems;
       c_feet += (unsigned long long)nitems;
