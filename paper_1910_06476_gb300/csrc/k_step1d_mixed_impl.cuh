@@ -12,7 +12,13 @@
 //   - the energy constraint (eq. remap_energy) is solved per element; its mismatch is formed
 //     from increments only, so that the decision to apply it is free of float cancellation;
 //   - the result is written back exactly as ref + psi by TwoSum (Knuth), hi = fl(ref + psi),
-//     lo = (ref + psi) - hi.
+//     lo = (ref + psi) - hi;
+//   - with the mass row (hard fit), the element's mass target is also formed in float-float,
+//     M^n - lam (F_own - F_up), where F is the outflow-flux functional applied to an element's hi + lo
+//     (each element's F is computed bit for bit alike by the element itself and by its downstream
+//     neighbour, so global mass telescopes); after the fit, the float-float miss of the written
+//     element mass is moved along the pseudo-inverse column of the mass row into the lo words, so
+//     that the element mass meets its target to about 1e-16 relative.
 // The kernel is persistent: a CTA advances tiles of TILE elements, one thread per element.  A
 // tile's rows (its elements and the upwind halo element) are one contiguous run of each plane;
 // one thread moves both runs into shared memory with bulk asynchronous copies (TMA) that complete
@@ -22,6 +28,7 @@
 // the CTA stops, reports SL_ST_TIMEOUT, and drains its stores.
 #include <algorithm>
 
+#include "ffloat.cuh"
 #include "sl_internal.h"
 
 namespace sl {
@@ -116,13 +123,35 @@ __device__ __forceinline__ TileGeo tile_geo(const Mixed1DParams& P, int t) {
   return g;
 }
 
+// The outflow flux functional of one element's row: ref sum(f) + sum_i f_i ((hi_i - ref) + lo_i)
+// with ref = hi_0, the same float operations whichever element evaluates it (the element itself or
+// its downstream neighbour), so that both see the same number
+template <int NN>
+__device__ __forceinline__ float row_flux(const float* f, float sumf, const float* hi, const float* lo) {
+  const float ref = hi[0];
+  float acc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NN; ++i) acc = fmaf(f[i], __fadd_rn(__fsub_rn(hi[i], ref), lo[i]), acc);
+  return fmaf(ref, sumf, acc);
+}
+
 // One element: rows own and up of the staged tile (shi, slo); writes res = phi^{n+1} - ref.
 // Returns false when the energy iteration did not converge (the linear solution is kept).
 template <int NN>
 __device__ __forceinline__ bool element_step(const Mixed1DParams& P, const float* shi, const float* slo, int own,
-                                             int up, bool has_up, float& ref, float (&res)[NN]) {
+                                             int up, bool has_up, float& ref, float (&res)[NN], ff& target) {
   bool ok = true;
   ref = shi[own];
+  if (P.refine) {
+    // M^{n+1} = M^n - lam (F_own - F_up) in float-float; the fluxes are exact floats by definition
+    cdot mn;
+#pragma unroll
+    for (int i = 0; i < NN; ++i) mn.add(P.wh[i], P.wl[i], shi[own + i], slo[own + i]);
+    const float fo = row_flux<NN>(P.Ff, P.sumf, shi + own, slo + own);
+    const float fu = has_up ? row_flux<NN>(P.Ff, P.sumf, shi + up, slo + up) : (float)P.ghost * P.sumf;
+    const ff net = two_sum(fo, -fu);
+    target = ff_add(mn.get(), ff_neg(ff_mul(net, ff{P.lam, P.lam_lo})));
+  }
   float ps[NN], pu[NN];
   if (has_up) {                             // own and upwind node i side by side (paired adds)
     const float2 mref = make_float2(-ref, -ref);
@@ -325,17 +354,19 @@ __global__ void __launch_bounds__(TILE, NN <= 11 ? 3 : 2)
     const bool active = e < K;
     float res[NN];
     float ref = 0.0f;
+    ff target = {0.0f, 0.0f};
     if (active) {
       const int own = g.sh + (P.left_up ? tid + 1 : tid) * NN;
       const int up = g.sh + (P.left_up ? tid : tid + 1) * NN;
       const bool has_up = wrap_elem(P.left_up ? e - 1 : e + 1, K, P.periodic != 0) >= 0;
-      if (!element_step<NN>(P, shi, slo, own, up, has_up, ref, res)) bits |= SL_ST_PICARD_NOCONV;
+      if (!element_step<NN>(P, shi, slo, own, up, has_up, ref, res, target)) bits |= SL_ST_PICARD_NOCONV;
     }
     __syncthreads();                              // the stage's rows are rewritten below
     if (active) {
       bool finite = true;
       // TwoSum: hi + lo == ref + res exactly; nodes j and j + 1 in paired operations
       // (a - b is formed as fma(b, -1, a), the same single rounding)
+      float vh[NN], vl[NN];
       const float2 rr = make_float2(ref, ref), m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
       for (int j = 0; j + 1 < NN; j += 2) {
@@ -344,20 +375,36 @@ __global__ void __launch_bounds__(TILE, NN <= 11 ? 3 : 2)
         const float2 bb = __ffma2_rn(rr, m1, s2);                  // s - ref
         const float2 t = __ffma2_rn(__ffma2_rn(bb, m1, s2), m1, rr);   // ref - (s - bb)
         const float2 err = __fadd2_rn(t, __ffma2_rn(bb, m1, r));    // + (res - bb)
-        shi[tid * NN + j] = s2.x;
-        shi[tid * NN + j + 1] = s2.y;
-        slo[tid * NN + j] = err.x;
-        slo[tid * NN + j + 1] = err.y;
-        finite = finite && isfinite(s2.x) && isfinite(s2.y);
+        vh[j] = s2.x;
+        vh[j + 1] = s2.y;
+        vl[j] = err.x;
+        vl[j + 1] = err.y;
       }
       if (NN & 1) {
         constexpr int j = NN - 1;
         const float s = ref + res[j];
         const float bb = s - ref;
-        const float err = (ref - (s - bb)) + (res[j] - bb);
-        shi[tid * NN + j] = s;
-        slo[tid * NN + j] = err;
-        finite = finite && isfinite(s);
+        vh[j] = s;
+        vl[j] = (ref - (s - bb)) + (res[j] - bb);
+      }
+      if (P.refine) {
+        // float-float miss of the element mass, moved along the mass column into the lo words
+        cdot mv;
+#pragma unroll
+        for (int i = 0; i < NN; ++i) mv.add(P.wh[i], P.wl[i], vh[i], vl[i]);
+        const float miss = ff_to_f(ff_add(target, ff_neg(mv.get())));
+#pragma unroll
+        for (int j = 0; j < NN; ++j) {
+          const ff v = fast_two_sum(vh[j], fmaf(miss, P.cmass[j], vl[j]));
+          vh[j] = v.hi;
+          vl[j] = v.lo;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NN; ++j) {
+        shi[tid * NN + j] = vh[j];
+        slo[tid * NN + j] = vl[j];
+        finite = finite && isfinite(vh[j]);
       }
       if (!finite) bits |= SL_ST_NONFINITE;
       fence_to_async();

@@ -16,6 +16,13 @@
 // halo element) is one contiguous run of global memory; it is copied in aligned 16-byte vectors
 // into a shared row buffer at the same offset modulo 16 bytes, followed by the y-upwind halo row.
 // Results are written back into the own slots and stored from there with aligned vectors.
+// With the mass row, the element's mass target is also formed in float-float: M^n (float-float sum of
+// w (x) w (hi + lo)) minus its outflow fluxes through the x- and y-outflow faces plus its upwind
+// neighbours' outflow fluxes, each flux a fixed float functional of one element's values evaluated
+// alike by that element and by its downstream neighbour (so global mass telescopes); after the fit
+// the float-float miss of the written element mass is moved along the mass column of the
+// pseudo-inverse into the lo words.
+#include "ffloat.cuh"
 #include "sl_internal.h"
 
 namespace sl {
@@ -57,6 +64,10 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
   __shared__ int64_t s_a0[TY + 1];                // first aligned global float of each staged row
   __shared__ int s_off[TY + 1], s_nv[TY + 1];     // row data offset in its buffer; vectors (0: gather)
   const int tid = threadIdx.x;
+  // mass refinement (dynamic shared memory): per element and row, the row partials of the own and
+  // upwind outflow fluxes and of M^n (slots 0-5), then per column the written mass (6, 7)
+  extern __shared__ __align__(16) float s_dyn[];
+  float (*s_fp)[NN][8] = reinterpret_cast<float (*)[NN][8]>(s_dyn);
   const int ex0 = blockIdx.x * TX, ey0 = blockIdx.y * TY;
   const bool perx = P.per_x != 0, pery = P.per_y != 0;
   const int xs0 = P.xw ? ex0 - 1 : ex0;           // first element of a staged tile row
@@ -165,6 +176,37 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
     s_v[el][j] = gy ? 0.0f : v;
     s_p[el][j] = pm;
   }
+  if (P.refine) {
+    // row j of: the own outflow fluxes (x, y faces), the upwind neighbours' outflow fluxes (their
+    // rows with their own references, in the same operations as they use themselves), the own mass
+    const float* Fx = tab + P.o_fx;
+    const float* Fy = tab + P.o_fy;
+    const float* Wh = tab + P.o_wh;
+    const float* Wl = tab + P.o_wl;
+    float fxo = 0.0f, fyo = 0.0f, fxu = 0.0f, fyu = 0.0f;
+    cdot mn;
+    const float refx = s_hi[sx], refy = s_hi[sy];
+#pragma unroll
+    for (int i = 0; i < NN; ++i) {
+      const float fxi = __ldg(Fx + i * NN + j), fyi = __ldg(Fy + i * NN + j);
+      const float hi = s_hi[so + j * NN + i], lo = s_lo[so + j * NN + i];
+      const float qo = __fadd_rn(__fsub_rn(hi, ref), lo);
+      const float qx = __fadd_rn(__fsub_rn(s_hi[sx + j * NN + i], refx), s_lo[sx + j * NN + i]);
+      const float qy = __fadd_rn(__fsub_rn(s_hi[sy + j * NN + i], refy), s_lo[sy + j * NN + i]);
+      fxo = fmaf(fxi, qo, fxo);
+      fyo = fmaf(fyi, qo, fyo);
+      fxu = fmaf(fxi, qx, fxu);
+      fyu = fmaf(fyi, qy, fyu);
+      mn.add(__ldg(Wh + i * NN + j), __ldg(Wl + i * NN + j), hi, lo);
+    }
+    const ff mnr = mn.get();
+    s_fp[el][j][0] = fxo;
+    s_fp[el][j][1] = fyo;
+    s_fp[el][j][2] = fxu;
+    s_fp[el][j][3] = fyu;
+    s_fp[el][j][4] = mnr.hi;
+    s_fp[el][j][5] = mnr.lo;
+  }
   // x-remap of row j: t[j][l] = sum_i R_x[l][i] psi[j][i]; rows l, l + 1 in paired FMAs (each
   // lane rounds like fmaf, in the same order)
 #pragma unroll
@@ -258,6 +300,7 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
     const float l0j = __ldg(tab + P.o_l0 + j), l1j = __ldg(tab + P.o_l1 + j);
     const float wj = __ldg(tab + P.o_w + j) * sm;
     bool finite = true;
+    float vh[NN], vl[NN];
     // nodes k and k + 1 in paired operations, each lane in the scalar order (a - b as fma(b, -1, a))
     const float2 rr = make_float2(ref, ref), m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
@@ -274,11 +317,10 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
       const float2 bb = __ffma2_rn(rr, m1, s2);                         // s - ref
       const float2 t = __ffma2_rn(__ffma2_rn(bb, m1, s2), m1, rr);      // ref - (s - bb)
       const float2 e = __fadd2_rn(t, __ffma2_rn(bb, m1, acc));          // + (acc - bb)
-      s_hi[so + k * NN + j] = s2.x;
-      s_hi[so + (k + 1) * NN + j] = s2.y;
-      s_lo[so + k * NN + j] = e.x;
-      s_lo[so + (k + 1) * NN + j] = e.y;
-      finite = finite && isfinite(s2.x) && isfinite(s2.y);
+      vh[k] = s2.x;
+      vh[k + 1] = s2.y;
+      vl[k] = e.x;
+      vl[k + 1] = e.y;
     }
     if (NN & 1) {
       constexpr int k = NN - 1;
@@ -292,10 +334,55 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
       }
       const float s = ref + acc;
       const float bb = s - ref;
-      const float e = (ref - (s - bb)) + (acc - bb);
-      s_hi[so + k * NN + j] = s;
-      s_lo[so + k * NN + j] = e;
-      finite = finite && isfinite(s);
+      vh[k] = s;
+      vl[k] = (ref - (s - bb)) + (acc - bb);
+    }
+    if (P.refine) {
+      // float-float mass of column j, summed over the columns by the element's first thread; the
+      // miss against the target goes along the mass column of the pseudo-inverse into the lo words
+      const float* Wh = tab + P.o_wh;
+      const float* Wl = tab + P.o_wl;
+      cdot mvc;
+#pragma unroll
+      for (int k = 0; k < NN; ++k) mvc.add(__ldg(Wh + k * NN + j), __ldg(Wl + k * NN + j), vh[k], vl[k]);
+      const ff mv = mvc.get();
+      s_fp[el][j][6] = mv.hi;
+      s_fp[el][j][7] = mv.lo;
+      __syncthreads();
+      // F(element) = ref sum(f) + the row partials added in row order: own fluxes with this element's
+      // reference, upwind fluxes with the neighbour's (or the ghost value); every thread of the
+      // element forms the target and the miss in the same order
+      float axo = 0.0f, ayo = 0.0f, axu = 0.0f, ayu = 0.0f;
+      ff mn = {0.0f, 0.0f}, tot = {0.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < NN; ++q) {
+        axo += s_fp[el][q][0];
+        ayo += s_fp[el][q][1];
+        axu += s_fp[el][q][2];
+        ayu += s_fp[el][q][3];
+        mn = ff_add(mn, ff{s_fp[el][q][4], s_fp[el][q][5]});
+        tot = ff_add(tot, ff{s_fp[el][q][6], s_fp[el][q][7]});
+      }
+      const float gh = (float)P.ghost;
+      const float Fxo = fmaf(ref, P.sfx, axo), Fyo = fmaf(ref, P.sfy, ayo);
+      const float Fxu = gx ? gh * P.sfx : fmaf(s_hi[sx], P.sfx, axu);
+      const float Fyu = gy ? gh * P.sfy : fmaf(s_hi[sy], P.sfy, ayu);
+      // M^{n+1} = M^n - (outflow) + (inflow), float-float
+      const ff tg = ff_add(mn, ff_add(two_sum(-Fxo, -Fyo), two_sum(Fxu, Fyu)));
+      const float miss = ff_to_f(ff_add(tg, ff_neg(tot)));
+      const float* Cm = tab + P.o_cm;
+#pragma unroll
+      for (int k = 0; k < NN; ++k) {
+        const ff v = fast_two_sum(vh[k], fmaf(miss, __ldg(Cm + k * NN + j), vl[k]));
+        vh[k] = v.hi;
+        vl[k] = v.lo;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NN; ++k) {
+      s_hi[so + k * NN + j] = vh[k];
+      s_lo[so + k * NN + j] = vl[k];
+      finite = finite && isfinite(vh[k]);
     }
     if (active && !finite) atomicOr(status, SL_ST_NONFINITE);
   }
@@ -342,7 +429,9 @@ __global__ void __launch_bounds__(Tile<NN, TX, TY>::NT)
 template <int NN, int TX, int TY>
 void launch(const Mixed2DConstParams& p, const float* tab, const float* in, float* out, unsigned* st, cudaStream_t s) {
   dim3 grid((p.kx + TX - 1) / TX, (p.ky + TY - 1) / TY);
-  k_step2d_shared<NN, TX, TY><<<grid, Tile<NN, TX, TY>::NT, 0, s>>>(p, tab, in, out, st);
+  const size_t dyn = p.refine ? (size_t)Tile<NN, TX, TY>::NE * NN * 8 * sizeof(float) : 0;
+  if (dyn) allow_dynamic_smem((const void*)k_step2d_shared<NN, TX, TY>, dyn);
+  k_step2d_shared<NN, TX, TY><<<grid, Tile<NN, TX, TY>::NT, dyn, s>>>(p, tab, in, out, st);
 }
 
 }  // namespace k2c

@@ -41,6 +41,7 @@
 #include <type_traits>
 
 #include "k_map2d.cuh"
+#include "ffloat.cuh"
 
 namespace sl {
 namespace k2m {
@@ -56,40 +57,6 @@ constexpr int SOLVE_CAP = 40;
 constexpr float SOLVE_RTOL = 3e-7f;          // target, relative to max |psi*|
 constexpr float SOLVE_STALL = 4e-6f;         // a residual that stops improving below this is the float floor
 constexpr float SOLVE_FLOOR = 1e-4f;         // best residual accepted (SL_ST_SOLVE_FLOOR) above the floor
-
-// ------------------------------------------------------------------ float-float arithmetic
-// Error-free transformations: Knuth's two-sum and the FMA product error.  A float-float value is the
-// unevaluated sum hi + lo with |lo| <= ulp(hi) / 2.
-struct ff {
-  float hi, lo;
-};
-__device__ __forceinline__ ff two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ ff fast_two_sum(float a, float b) {   // |a| >= |b| or a = 0
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ff two_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return {p, fmaf(a, b, -p)};
-}
-// sum of two float-float values; symmetric in its arguments bit for bit (the two-sum error term is
-// exact whatever the order), so a butterfly leaves the same value in every lane
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const ff s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo));
-}
-__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
-// product with a float-float weight, to about 2^-44 relative
-__device__ __forceinline__ ff ff_mul(ff a, ff w) {
-  const ff p = two_prod(a.hi, w.hi);
-  return fast_two_sum(p.hi, fmaf(a.hi, w.lo, fmaf(a.lo, w.hi, p.lo)));
-}
-__device__ __forceinline__ float ff_to_f(ff a) { return __fadd_rn(a.hi, a.lo); }
 
 // asynchronous 4-byte global-to-shared copies (the next element's inputs are staged while the current
 // one is computed); a thread waits for its own copies, a group barrier then publishes them

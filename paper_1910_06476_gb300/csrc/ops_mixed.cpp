@@ -150,6 +150,29 @@ bool build_mixed1d(const sl_ctx* c, const FitOps& fit, double a, double dt, unsi
   for (int k = 0; k < m * n; ++k) P.C[k] = (float)C[k];
   if (fitmode == SL_FIT_HARD)
     for (int k = 0; k < n * m; ++k) P.Cp[k] = (float)fit.Cpinv[k];
+  // the refinement moves mass along C+ e_m, which keeps the other rows only when C C+ e_m = e_m
+  // (the mass row independent of the face rows: n >= 3)
+  bool indep = false;
+  if (fitmode == SL_FIT_HARD && (cons & SL_C_MASS)) {
+    ld dev = 0.0L;
+    for (int k = 0; k < m; ++k) {
+      ld acc = 0.0L;
+      for (int j = 0; j < n; ++j) acc += (ld)fit.C[k * n + j] * (ld)fit.Cpinv[j * m + (m - 1)];
+      dev = std::max(dev, std::fabs(acc - (k == m - 1 ? 1.0L : 0.0L)));
+    }
+    indep = dev < 1e-9L;
+  }
+  P.refine = indep ? 1 : 0;
+  P.lam_lo = (float)(lam - (ld)P.lam);
+  float sumf = 0.0f;
+  for (int j = 0; j < n; ++j) {
+    P.Ff[j] = (float)f[j];
+    sumf += P.Ff[j];
+    P.wh[j] = (float)b.w[j];
+    P.wl[j] = (float)(b.w[j] - (double)P.wh[j]);
+    P.cmass[j] = P.refine ? (float)fit.Cpinv[j * m + (m - 1)] : 0.0f;
+  }
+  P.sumf = sumf;
   return true;
 }
 

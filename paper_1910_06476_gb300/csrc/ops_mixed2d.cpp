@@ -182,6 +182,55 @@ bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigne
   P.o_l0 = put(l0);
   P.o_l1 = put(l1);
   P.o_w = put(w);
+  // mass refinement: each element's outflow flux through its x- and y-outflow faces is a fixed
+  // float functional of its own values (lam Kx, lam Ky), evaluated alike by the element and by its
+  // downstream neighbour; w (x) w in float-float; the mass column of C+
+  // the refinement moves mass along C+ e_m, which keeps the face rows only when C C+ e_m = e_m
+  bool indep = false;
+  if (mass) {
+    const int rm = bnd ? 4 * n : 0;
+    ld dev = 0.0L;
+    for (int k = 0; k < m; ++k) {
+      ld acc = 0.0L;
+      for (int q = 0; q < nd; ++q) acc += (ld)F.C[(size_t)k * nd + q] * (ld)F.Cpinv[(size_t)q * m + rm];
+      dev = std::max(dev, std::fabs(acc - (k == rm ? 1.0L : 0.0L)));
+    }
+    indep = dev < 1e-9L;
+  }
+  P.refine = indep ? 1 : 0;
+  if (indep) {
+    std::vector<ld> fx(nd), fy(nd), wh(nd), wl(nd), cm(nd);
+    float sfx = 0.0f, sfy = 0.0f;
+    for (int k = 0; k < nd; ++k) {
+      fx[k] = (ld)(float)(lam * Kx[k]);
+      fy[k] = (ld)(float)(lam * Ky[k]);
+    }
+    // the sums in the order the kernel forms a row's partial sums and then adds the rows
+    for (int j = 0; j < n; ++j) {
+      float rx = 0.0f, ry = 0.0f;
+      for (int i = 0; i < n; ++i) {
+        rx += (float)fx[j * n + i];
+        ry += (float)fy[j * n + i];
+      }
+      sfx += rx;
+      sfy += ry;
+    }
+    P.sfx = sfx;
+    P.sfy = sfy;
+    const int rmass = bnd ? 4 * n : 0;
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) {
+        const double v = B.w[i] * B.w[j];
+        wh[j * n + i] = (ld)(float)v;
+        wl[j * n + i] = (ld)(float)(v - (double)(float)v);
+        cm[j * n + i] = (ld)F.Cpinv[(size_t)(j * n + i) * m + rmass];
+      }
+    P.o_fx = put(transpose(fx));
+    P.o_fy = put(transpose(fy));
+    P.o_wh = put(transpose(wh));
+    P.o_wl = put(transpose(wl));
+    P.o_cm = put(cm);                          // [k][j]: node (j, k) of column j at k n + j
+  }
   buf.resize((buf.size() + 3) & ~size_t(3), 0.0f);
   return true;
 }

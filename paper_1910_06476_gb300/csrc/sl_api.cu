@@ -209,6 +209,20 @@ int persistent_grid(const void* kernel, int threads, size_t smem) {
   cache.emplace(key, grid);
   return grid;
 }
+void allow_dynamic_smem(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*>, size_t> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = done[std::make_tuple(dev, kernel)];
+  if (bytes <= have) return;
+  // a failure is cleared here and shows as a failed launch, which is checked when enqueued
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+    cudaGetLastError();
+  else
+    have = bytes;
+}
 }  // namespace sl
 
 namespace {

@@ -174,6 +174,12 @@ struct Mixed2DConstParams {
   int o_RxT, o_RyT;                         // transposed remap matrices
   int o_g;                                  // face rows of (C C^T)^+ over the kept residuals
   int o_l0, o_l1, o_w;                      // l0, l1, w again, read per thread
+  // float-float mass refinement (with the mass row): lam times the outflow-flux functionals of an
+  // element's own data through its x- and y-outflow faces ([i][j] tables, row j read by thread j)
+  // and their sums; w_i w_j as float-float ([i][j]); the mass column of the pseudo-inverse ([k][j])
+  int refine;
+  float sfx, sfy;
+  int o_fx, o_fy, o_wh, o_wl, o_cm;
 };
 bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigned cons, int rk,
                          std::vector<float>& buf, Mixed2DConstParams& P, std::string& err);
@@ -195,6 +201,12 @@ struct Mixed1DParams {
   float E[3][NMAX];                      // basis at the characteristic feet of the outflow face
   float C[MMAX1D * NMAX];                // linear constraint rows
   float Cp[NMAX * MMAX1D];               // their pseudo-inverse (hard fit)
+  // float-float mass refinement (hard fit with the mass row): the outflow-flux functional
+  // f = sum_s fb_s E_s, its sum, lam as float-float, the weights as float-float and the column of
+  // the pseudo-inverse that belongs to the mass row
+  int refine;
+  float lam_lo, sumf;
+  float Ff[NMAX], wh[NMAX], wl[NMAX], cmass[NMAX];
 };
 
 bool build_mixed1d(const sl_ctx* c, const FitOps& fit, double a, double dt, unsigned cons, int rk, int fitmode,
@@ -205,6 +217,9 @@ void launch_pack(int64_t nvals, int64_t plane, const double* src, float* dst, cu
 // after raising the kernel's dynamic shared-memory limit to smem) times the SM count; cached per
 // (device, kernel, threads, smem) under a lock, so host threads on several devices may launch at once.
 int persistent_grid(const void* kernel, int threads, size_t smem);
+// Raise a kernel's dynamic shared-memory allowance on the current device to bytes (once per device,
+// kernel and size; needed when its static plus dynamic shared memory exceeds 48 KB).
+void allow_dynamic_smem(const void* kernel, size_t bytes);
 void launch_unpack(int64_t nvals, int64_t plane, const float* src, double* dst, cudaStream_t s);
 
 // float offset of the lo plane of a double-float state of nvals nodes: 256-byte aligned

@@ -110,8 +110,11 @@ def test_mixed_1000_steps_vs_fp64(sl, n, cons):
             errs[s + 1] = (d.norm() / a64.norm()).item()
     assert c64.sync() == 0 and cm.sync() == 0
     assert errs[1] <= TOL_MIXED and errs[1000] <= TOL_MIXED, errs
-    # periodic mass: FP64 keeps it to round-off; the mixed path to float rounding of increments
-    assert abs(cm.mass(am) - c64.mass(a64)) < 1e-8 * abs(c64.mass(a64))
+    # periodic mass, conserved to round-off by both paths: FP64 by telescoping face fluxes, the
+    # mixed path by its float-float mass targets and refinement
+    m0 = cm.mass(cm.pack(phi))
+    assert abs(c64.mass(a64) - m0) < 1e-12 * abs(m0)
+    assert abs(cm.mass(am) - m0) < 1e-12 * abs(m0), (cm.mass(am) - m0) / m0
 
 
 def test_mixed_full_size_sampled(sl):

@@ -119,7 +119,8 @@ def test_mixed2d_config3_500_steps(sl):
     c64, cm, a64, am, errs, m0 = _long_run(sl, prob, 9, 500, sl.VEL_CONST, (1.0, 0.5))
     assert c64.sync() == 0 and cm.sync() == 0
     assert errs[1] <= TOL and errs[500] <= TOL, errs
-    assert abs(cm.mass(am) - m0) <= 1e-9
+    # periodic mass to round-off (the data have zero mean: an absolute bound on a unit square)
+    assert abs(cm.mass(am) - m0) <= 1e-13, cm.mass(am) - m0
 
 
 def test_mixed2d_swirl_against_fp64(sl):
