@@ -691,13 +691,23 @@ def element_step_2d(setup, phi, ex, ey, o, phihat_cache=None):
             xf, yf, nrm, _ = _face_points(setup, ex, ey, face, n)
             u, v, _ = velocity(o.vel, xf, yf, tn1)
             un = u * nrm[0] + v * nrm[1]
-            own = poly_2d(setup, ph, ex, ey, xf, yf)           # eq. 2dx/2dy_bnd_interpolate
             nb = _nb_2d(setup, ex, ey, face)
+            if o.bvalue == BV_BACKTRACK:
+                # eq. 4.11 on each face point: phi^n of the element (and of the neighbour, in its
+                # own frame) at the backward characteristic foot, over the divergence factor
+                fx, fy, fac = rk_particles(o.vel, xf, yf, np.ones(n), tn1, -o.dt, o.rk_order)
+                own = poly_2d(setup, _get(phi, ex, ey).astype(np.float64), ex, ey, fx, fy) / fac
+            else:
+                own = poly_2d(setup, ph, ex, ey, xf, yf)       # eq. 2dx/2dy_bnd_interpolate
             if nb is None:
                 other = _ghost(setup, xf, yf, tn1)
             else:
                 sx, sy = _periodic_shift(setup, ex, ey, face, nb)
-                other = poly_2d(setup, phihat_of(*nb), nb[0], nb[1], xf + sx, yf + sy)
+                if o.bvalue == BV_BACKTRACK:
+                    other = poly_2d(setup, _get(phi, *nb).astype(np.float64), nb[0], nb[1], fx + sx,
+                                    fy + sy) / fac
+                else:
+                    other = poly_2d(setup, phihat_of(*nb), nb[0], nb[1], xf + sx, yf + sy)
             for q in range(n):
                 # row: trace of the unknown polynomial at this face point
                 if face in (0, 1):

@@ -248,13 +248,30 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb
   if (!solved && tid == 0) atomicOr(status, SL_ST_SOLVE_NOCONV);
   if (part) W.phihat[E.base + tid] = s_ph[tid];
 
-  // traces of phihat at the four faces, thread (face, q)
+  // interface values at the face points, thread (face, q): traces of phihat (eq. 2dx/2dy_bnd_interpolate),
+  // or phi^n at the backward characteristic foot of the face point from t^{n+1} (eq. 4.11)
   if (tid < 4 * NN) {
     const int f = tid / NN, q = tid % NN;
-    const double* L = (f == 1 || f == 3) ? s_l1 : s_l0;
     double acc = 0.0;
+    if (P.bvalue == SL_BV_BACKTRACK) {
+      double fx = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
+      double fy = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
+      rk2d(P, fx, fy, P.t + P.dt, -P.dt);
+      double bx[NN], by[NN];
+      basis_at<NN>(s_xi, s_lam, (fx - x0) / hx, bx);
+      basis_at<NN>(s_xi, s_lam, (fy - y0) / hy, by);
+#pragma unroll 1
+      for (int mm = 0; mm < NN; ++mm) {
+        double row = 0.0;
 #pragma unroll
-    for (int k = 0; k < NN; ++k) acc += (f < 2 ? s_ph[q * NN + k] : s_ph[k * NN + q]) * L[k];
+        for (int l = 0; l < NN; ++l) row += s_phi[mm * NN + l] * bx[l];
+        acc += by[mm] * row;
+      }
+    } else {
+      const double* L = (f == 1 || f == 3) ? s_l1 : s_l0;
+#pragma unroll
+      for (int k = 0; k < NN; ++k) acc += (f < 2 ? s_ph[q * NN + k] : s_ph[k * NN + q]) * L[k];
+    }
     W.traces[E.g * M.tstride + tid] = acc;
   }
   // outflow fluxes: for each face point and RK stage where u.n_out > TIE, phi^n at the foot.
@@ -368,8 +385,17 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, Tables1D tb
     if (un > TIE) val = own;
     else if (un < -TIE) val = other;
     else val = nb < 0 ? own : 0.5 * (own + other);
+    // the row's value at phihat: the own trace when the interface values are traces of phihat,
+    // else the trace formed here
+    double trh = own;
+    if (P.bvalue == SL_BV_BACKTRACK) {
+      const double* L = (f == 1 || f == 3) ? s_l1 : s_l0;
+      trh = 0.0;
+#pragma unroll
+      for (int k = 0; k < NN; ++k) trh += (f < 2 ? s_ph[q * NN + k] : s_ph[k * NN + q]) * L[k];
+    }
     s_d[tid] = val;
-    s_r[tid] = val - own;                     // the row's value at phihat is exactly the own trace
+    s_r[tid] = val - trh;
   }
   // mass and energy targets (reference measure)
   double Et = 0.0;

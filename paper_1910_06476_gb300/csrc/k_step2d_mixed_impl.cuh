@@ -858,13 +858,35 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB)
       el[5] = Mn.hi;
       el[6] = Mn.lo;
     }
-    // traces of psihat (relative to L)
+    // interface values at the face points (relative to L): traces of psihat, or phi^n at the
+    // backward characteristic foot of the face point from t^{n+1} (eq. 4.11; meshes of one node
+    // count), L(foot) - L(face point) being the linear part over the foot's displacement
     if (t < 4 * NN) {
       const int f = t / NN, q = t % NN;
-      const float* Lb = (f == 1 || f == 3) ? s_l1 : s_l0;
       float acc = 0.0f;
+      if (P.bvalue == SL_BV_BACKTRACK) {
+        const float xr = f == 0 ? 0.0f : f == 1 ? 1.0f : s_xi[q];
+        const float yr = f == 2 ? 0.0f : f == 3 ? 1.0f : s_xi[q];
+        float Sx = 0.0f, Cx = 0.0f, Sy = 0.0f, Cy = 0.0f;
+        if (V.kind == SL_VEL_SWIRL && !V.direct) {
+          Sx = f < 2 ? sm.T.corner[f] : sm.T.n[0][q];
+          Cx = f < 2 ? sm.T.corner[4 + f] : sm.T.n[1][q];
+          Sy = f < 2 ? sm.T.n[2][q] : sm.T.corner[f];
+          Cy = f < 2 ? sm.T.n[3][q] : sm.T.corner[4 + f];
+        }
+        float fdx = 0.0f, fdy = 0.0f;
+        rk_disp(V, P.rk, xr, yr, Sx, Cx, Sy, Cy, fdx, fdy, -X.dt, 1.0f, -1.0f, sm.T.ct);
+        float bx[NN], by[NN];
+        basis_at<NN>(s_xi, s_lam, xr, fdx, bx);
+        basis_at<NN>(s_xi, s_lam, yr, fdy, by);
 #pragma unroll
-      for (int kk = 0; kk < NN; ++kk) acc = fmaf(f < 2 ? sm.ph[q * NP + kk] : sm.ph[kk * NP + q], Lb[kk], acc);
+        for (int mm = 0; mm < NN; ++mm) acc = fmaf(by[mm], row_dot<NN>(sm.psi + mm * NP, bx), acc);
+        acc += fmaf(gx, fdx, gy * fdy);
+      } else {
+        const float* Lb = (f == 1 || f == 3) ? s_l1 : s_l0;
+#pragma unroll
+        for (int kk = 0; kk < NN; ++kk) acc = fmaf(f < 2 ? sm.ph[q * NP + kk] : sm.ph[kk * NP + q], Lb[kk], acc);
+      }
       W.traces[E.g * M.tstride + t] = acc;
     }
     // outflow over each face and step; a face shared with a neighbour of another node count takes
@@ -1212,7 +1234,17 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2)
       if (un > (float)TIE) val = own;
       else if (un < -(float)TIE) val = other;
       else val = nb < 0 ? own : 0.5f * (own + other);
-      sm.r[t] = val - own;
+      // the row's value at psihat: the own trace when the interface values are traces of psihat,
+      // else the trace formed here from the stored psihat
+      float trh = own;
+      if (P.bvalue == SL_BV_BACKTRACK) {
+        const float* Lb = (f == 1 || f == 3) ? s_l1 : s_l0;
+        const float* ps = W.psihat + E.base;
+        trh = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < NN; ++kk) trh = fmaf(f < 2 ? ps[q * NN + kk] : ps[kk * NN + q], Lb[kk], trh);
+      }
+      sm.r[t] = val - trh;
     }
     // net outflow of mass (increments), of the squared increments and of the velocity, lanes 0-3 of
     // the first warp one face each, summed in face order; the float-float mass target

@@ -743,8 +743,8 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
     c->mix.picard_cap = P.picard_cap;
     launch_step1d_mixed(c->mix, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream);
   } else if (M.dim == 2 && c->precision == SL_FP64) {
-    if (opt->bvalue != SL_BV_INTERP)
-      return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
+    if (opt->bvalue != SL_BV_INTERP && c->mapped)
+      return fail(c, SL_EUNSUPPORTED, "backtracked interface values need a mesh of one node count");
     const sl_status st = step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
     if (st != SL_OK) return st;
   } else if (uses_m2c(c, vel, opt)) {
@@ -754,8 +754,8 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
     c->m2c.plane = plane_stride(c->nvals);
     launch_step2d_const(c->m2c, c->d_m2c, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream);
   } else if (M.dim == 2 && c->precision == SL_MIXED) {
-    if (opt->bvalue != SL_BV_INTERP)
-      return fail(c, SL_EUNSUPPORTED, "2D interface values are interpolated (eq. 2dx/2dy_bnd_interpolate)");
+    if (opt->bvalue != SL_BV_INTERP && c->mapped)
+      return fail(c, SL_EUNSUPPORTED, "backtracked interface values need a mesh of one node count");
     if (opt->fit != SL_FIT_HARD) return fail(c, SL_EUNSUPPORTED, "the 2D mixed path uses the hard fit");
     const sl_status st = step2d_general(c, P, vel, t, dt, opt, phi_in, phi_out);
     if (st != SL_OK) return st;

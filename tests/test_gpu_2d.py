@@ -29,7 +29,8 @@ def vel_pair(sl, kind, p):
     return sl.velocity(kind, *p), O.Vel(kind, tuple(p) + (0,) * (6 - len(p)))
 
 
-def run_case(sl, kx, ky, n, kind, p, bc, cons, rk=4, fit=0, basis=0, ghost=0.0, data=None, t=0.3, seed=0):
+def run_case(sl, kx, ky, n, kind, p, bc, cons, rk=4, fit=0, basis=0, ghost=0.0, data=None, t=0.3, seed=0,
+             bvalue=0):
     box = (0.0, 1.0, 0.0, 1.0)
     ctx = sl.Context(2, kx, ky, box, n, basis, sl.FP64, (bc,) * 4, ghost)
     setup = O.Setup(2, kx, ky, box, n, basis, (bc,) * 4, ghost)
@@ -42,10 +43,10 @@ def run_case(sl, kx, ky, n, kind, p, bc, cons, rk=4, fit=0, basis=0, ghost=0.0, 
     dt = ctx.max_dt(gv)
     a = torch.tensor(phi.ravel(), device="cuda")
     b = torch.empty_like(a)
-    ctx.step(a, b, gv, t, dt, sl.options(cons, rk, fit))
+    ctx.step(a, b, gv, t, dt, sl.options(cons, rk, fit, bvalue))
     bits = ctx.sync()
     got = b.cpu().numpy().reshape(ky, kx, n, n)
-    ref, infos = O.step_2d(setup, phi, O.StepOpts(ov, t, dt, cons, rk, fit))
+    ref, infos = O.step_2d(setup, phi, O.StepOpts(ov, t, dt, cons, rk, fit, bvalue))
     conv = np.array([[infos[(ex, ey)]["converged"] for ex in range(kx)] for ey in range(ky)])
     return setup, got, ref, conv, bits
 
@@ -94,6 +95,41 @@ def test_2d_step_parity(sl, case):
     kx, ky, n, kind, p, bc, cons, rk, fit, basis = case
     r = run_case(sl, kx, ky, n, kind, p, bc, cons, rk, fit, basis, ghost=0.2 if bc else 0.0, seed=kx * 7 + n)
     check(*r, sl)
+
+
+BT_CASES = [
+    # kx, ky, n, kind, params, bc, cons, rk, fit, basis: backtracked interface values (eq. 4.11)
+    (6, 5, 9, 0, (1.0, 0.5), 0, 3, 4, 0, 0),
+    (4, 4, 5, 0, (-0.8, 0.6), 0, 7, 4, 0, 0),
+    (4, 3, 4, 0, (0.7, -0.4), 0, 1, 2, 1, 0),         # soft fit, second order
+    (5, 4, 6, 0, (1.0, 0.0), 0, 3, 4, 0, 1),          # axis-aligned, Chebyshev-Gauss
+    (1, 1, 7, 0, (1.0, 0.5), 0, 3, 4, 0, 0),          # single element wrapping onto itself
+    (6, 6, 6, 1, (2 * np.pi, 0.5, 0.5), 1, 3, 4, 0, 0),   # rotation, inflow ghost
+    (5, 5, 8, 2, (5.0,), 1, 7, 4, 0, 0),              # swirl, mass + energy
+    (5, 5, 8, 2, (5.0,), 0, 3, 3, 0, 0),              # swirl, periodic, third order
+    (2, 2, 16, 1, (2 * np.pi, 0.5, 0.5), 1, 3, 4, 0, 0),
+]
+
+
+@pytest.mark.parametrize("case", BT_CASES, ids=[f"{c[0]}x{c[1]}n{c[2]}v{c[3]}bc{c[5]}c{c[6]}rk{c[7]}"
+                                                for c in BT_CASES])
+def test_2d_backtracked_interface_parity(sl, case):
+    kx, ky, n, kind, p, bc, cons, rk, fit, basis = case
+    r = run_case(sl, kx, ky, n, kind, p, bc, cons, rk, fit, basis, ghost=0.2 if bc else 0.0, seed=kx * 5 + n,
+                 bvalue=sl.BV_BACKTRACK)
+    check(*r, sl)
+
+
+def test_2d_backtracked_differs_from_interpolated(sl):
+    """The two interface rules give different steps on under-resolved data (the GPU takes the
+    rule it is given), and the same step on data the element polynomials hold exactly."""
+    a = run_case(sl, 4, 4, 5, 2, (5.0,), 0, 3, bvalue=sl.BV_INTERP, seed=3)
+    b = run_case(sl, 4, 4, 5, 2, (5.0,), 0, 3, bvalue=sl.BV_BACKTRACK, seed=3)
+    assert np.abs(a[1] - b[1]).max() > 1e-6
+    lin = lambda x, y: 1.0 + 0.3 * x - 0.2 * y
+    a = run_case(sl, 4, 4, 5, 0, (0.6, 0.3), 0, 3, data=lin, bvalue=sl.BV_INTERP)
+    b = run_case(sl, 4, 4, 5, 0, (0.6, 0.3), 0, 3, data=lin, bvalue=sl.BV_BACKTRACK)
+    assert np.abs(a[1] - b[1]).max() < 1e-12
 
 
 def test_2d_cosine_bell_and_hill_data(sl):

@@ -87,6 +87,60 @@ def test_mixed2d_step_parity(sl, case):
     assert rel(got, ref) <= TOL
 
 
+BT_CASES = [
+    # kx, ky, n, kind, params, bc, cons, rk, data: backtracked interface values (eq. 4.11); the
+    # shared-operator kernel leaves these to the general one
+    (6, 5, 9, 0, (1.0, 0.5), 0, 3, 4, "sincos"),
+    (4, 4, 5, 0, (-0.8, 0.6), 0, 7, 4, "sincos"),
+    (5, 4, 6, 0, (1.0, 0.0), 0, 3, 4, "sincos"),
+    (1, 1, 7, 0, (1.0, 0.5), 0, 3, 4, "sincos"),
+    (6, 6, 6, 1, (2 * np.pi, 0.5, 0.5), 1, 3, 4, "hill"),
+    (5, 5, 8, 2, (5.0,), 1, 7, 4, "bell"),
+    (5, 5, 8, 2, (5.0,), 0, 3, 4, "sincos"),
+    (3, 3, 12, 1, (2 * np.pi, 0.5, 0.5), 1, 3, 3, "sincos"),
+    (2, 2, 16, 0, (0.6, 0.9), 0, 3, 2, "sincos"),
+]
+
+
+@pytest.mark.parametrize("case", BT_CASES, ids=[f"{c[0]}x{c[1]}n{c[2]}v{c[3]}c{c[6]}{c[8]}" for c in BT_CASES])
+def test_mixed2d_backtracked_interface_parity(sl, case):
+    kx, ky, n, kind, p, bc, cons, rk, data = case
+    box = (0.0, 1.0, 0.0, 1.0)
+    ctx = sl.Context(2, kx, ky, box, n, 0, sl.MIXED, (bc,) * 4, 0.1 if bc else 0.0)
+    setup = O.Setup(2, kx, ky, box, n, 0, (bc,) * 4, 0.1 if bc else 0.0)
+    gv = sl.velocity(kind, *p)
+    ov = O.Vel(kind, tuple(p) + (0,) * (6 - len(p)))
+    x, y = ctx.node_coords()
+    phi = DATA[data](x, y) + 0.02 * sl_inputs.random_state(x.shape, kx + 2 * n)
+    dt = ctx.max_dt(gv)
+    a = ctx.pack(torch.tensor(phi.ravel(), device="cuda"))
+    b = ctx.new_state()
+    ctx.step(a, b, gv, 0.3, dt, sl.options(cons, rk, bvalue=sl.BV_BACKTRACK))
+    bits = ctx.sync()
+    got = ctx.unpack(b).cpu().numpy().reshape(ky, kx, n, n)
+    ref, infos = O.step_2d(setup, phi, O.StepOpts(ov, 0.3, dt, cons, rk, bvalue=O.BV_BACKTRACK,
+                                                  energy_skip_rtol=MIXED_SKIP))
+    conv = np.array([[infos[(ex, ey)]["converged"] for ex in range(kx)] for ey in range(ky)])
+    assert conv.all()
+    assert bits == 0, bits
+    assert rel(got, ref) <= TOL
+
+
+def test_mixed2d_backtracked_mass_to_roundoff(sl):
+    """Backtracked interface values leave the mass targets' telescoping alone: 200 periodic
+    swirl steps keep the global mass to round-off."""
+    ctx = sl.Context(2, 8, 8, (0.0, 1.0, 0.0, 1.0), 8, 0, sl.MIXED, (0,) * 4, 0.0)
+    gv = sl.velocity(sl.VEL_SWIRL, 5.0)
+    x, y = ctx.node_coords()
+    phi = torch.tensor((1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)).ravel(), device="cuda")
+    a, b = ctx.pack(phi), ctx.new_state()
+    m0 = ctx.mass(a)
+    dt = ctx.max_dt(gv, sl.RULE_PAPER)
+    out = ctx.run(a, b, gv, 0.0, dt, 200, sl.options(sl.C_BOUNDARY | sl.C_MASS, 4, bvalue=sl.BV_BACKTRACK))
+    assert ctx.sync() & ~sl.ST_PICARD_NOCONV == 0
+    assert abs(ctx.mass(out) - m0) <= 1e-12 * abs(m0)
+
+
 def _long_run(sl, prob, n, steps, kind, p):
     c64 = sl.Context(2, prob.kx, prob.ky, prob.box, n, 0, sl.FP64, prob.bc, prob.ghost)
     cm = sl.Context(2, prob.kx, prob.ky, prob.box, n, 0, sl.MIXED, prob.bc, prob.ghost)

@@ -146,6 +146,49 @@ def test_2d_exact_translation(fit):
     np.testing.assert_allclose(out, exact, atol=1e-12)
 
 
+@pytest.mark.parametrize("fit", [O.FIT_HARD, O.FIT_SOFT])
+@pytest.mark.parametrize("basis", [O.GAUSS_LEGENDRE, O.CHEB_GAUSS])
+@pytest.mark.parametrize("ab", [(0.8, 0.45), (-0.6, 0.7)])
+def test_2d_exact_translation_backtracking(fit, basis, ab):
+    """Backtracked interface values (eq. 4.11) in 2D: phi^n at the backward foot of each face
+    point is the exact solution there for translated polynomial data, so the step is the exact
+    translate, in both fits, both node families and both flow directions."""
+    n = 5
+    a, b = ab
+    vel = O.Vel(O.VEL_CONST, (a, b, 0, 0, 0, 0))
+    s = O.Setup(2, 3, 3, (0, 1, 0, 1), n, basis, (O.BC_INFLOW,) * 4,
+                lambda x, y, t: poly2(np.asarray(x) - a * t, np.asarray(y) - b * t))
+    phi = O.project_2d(s, poly2)
+    dt = O.max_dt(s, vel)
+    out, _ = O.step_2d(s, phi, O.StepOpts(vel, 0.0, dt, O.C_BOUNDARY | O.C_MASS, 4, fit, bvalue=O.BV_BACKTRACK))
+    exact = O.project_2d(s, lambda x, y: poly2(x - a * dt, y - b * dt))
+    np.testing.assert_allclose(out, exact, atol=1e-12)
+
+
+def test_2d_backtracking_differs_from_interpolation_on_rough_data():
+    """On data the remap cannot represent exactly the two interface-value rules differ (so the
+    pin above is not passed by the interpolated values by accident), and the backtracked values
+    equal the element's own phi^n evaluated at the feet."""
+    n = 4
+    vel = O.Vel(O.VEL_ROTATION, (2 * np.pi, 0.5, 0.5, 0, 0, 0))
+    s = O.Setup(2, 3, 3, (0, 1, 0, 1), n, O.GAUSS_LEGENDRE, (O.BC_INFLOW,) * 4, 0.0)
+    phi = 1.0 + 0.3 * np.random.default_rng(3).uniform(-1, 1, (3, 3, n, n))
+    dt = O.max_dt(s, vel, rule="paper")
+    oi = O.StepOpts(vel, 0.1, dt, O.C_BOUNDARY, 4)
+    ob = O.StepOpts(vel, 0.1, dt, O.C_BOUNDARY, 4, bvalue=O.BV_BACKTRACK)
+    _, ii = O.step_2d(s, phi, oi, elements=[(1, 1)])
+    _, ib = O.step_2d(s, phi, ob, elements=[(1, 1)])
+    assert np.max(np.abs(ii[(1, 1)]["d"] - ib[(1, 1)]["d"])) > 1e-6
+    # the E face (x = 2/3): points where the flow leaves take phi^n of element (1, 1) at the foot
+    xf, yf, nrm, _ = O._face_points(s, 1, 1, 1, n)
+    u, v, _ = O.velocity(vel, xf, yf, 0.1 + dt)
+    fx, fy, _ = O.rk_particles(vel, xf, yf, np.ones(n), 0.1 + dt, -dt, 4)
+    own = O.poly_2d(s, phi[1, 1], 1, 1, fx, fy)
+    out_pts = u * nrm[0] + v * nrm[1] > O.TIE
+    assert out_pts.any()
+    np.testing.assert_allclose(ib[(1, 1)]["d"][n:2 * n][out_pts], own[out_pts], atol=1e-13)
+
+
 def test_1d_constraints_hold_to_roundoff():
     rng = np.random.default_rng(11)
     s = O.Setup(1, 6, 1, (0, 1, 0, 0), 7)
