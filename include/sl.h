@@ -172,6 +172,22 @@ sl_status sl_step(sl_ctx* ctx, const void* phi_in, void* phi_out, const sl_veloc
 sl_status sl_run(sl_ctx* ctx, void* phi_a, void* phi_b, const sl_velocity* vel, double t0, double dt,
                  int nsteps, const sl_options* opt);
 
+/* Time-dependent inflow (Dirichlet) data for the domain faces of a 1D FP64 context (Sec. 5.1,
+ * the Dirichlet-versus-periodic comparison: the exact solution prescribed at the inflow; Sec. 4.3,
+ * boundary conditions through a specified ghost solution).  values is a DEVICE array of doubles
+ * owned by the caller, which must keep it alive and unchanged while steps that read it are in
+ * flight; NULL returns to the mesh's constant ghost.  One record per step, of SL_INFLOW_RECORD
+ * doubles: record[side * 5 + 0] is the ghost value at face `side` (0: x = x0, 1: x = x1) at
+ * t + dt, where it enters the upwind value of eq. 4.12a; record[side * 5 + 1 + s] is the value
+ * at t + c_s dt, the time of RK stage s (s < rk_order), where it enters the inflow flux of the
+ * mass and energy targets (eq. remap_mass, remap_energy).  Only inflow faces (SL_BC_INFLOW on
+ * that side) read it.  sl_step reads record 0; step k of sl_run reads the record at
+ * values + k * step_stride (step_stride >= SL_INFLOW_RECORD when nsteps > 1; a graph recorded by
+ * sl_run keeps the pointer it was recorded with).  Errors: SL_EINVAL for a negative stride,
+ * SL_EUNSUPPORTED for a 2D, mixed-precision or batch context (nothing is changed). */
+#define SL_INFLOW_RECORD 10
+sl_status sl_set_inflow(sl_ctx* ctx, const double* values, int64_t step_stride);
+
 /* Advance nsteps steps from t0 with a fixed dt, starting from and ending in HOST buffers of
  * sl_state_size doubles (node values in state layout, whatever the precision): copies host_in
  * to the device (converting to the state format), steps, converts back and copies the result

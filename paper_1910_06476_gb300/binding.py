@@ -17,6 +17,7 @@ SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ECFL, SL_EDEVICE, SL_EUNSUPPORTED = ra
 GAUSS_LEGENDRE, CHEB_GAUSS = 0, 1
 FP64, MIXED = 0, 1
 BC_PERIODIC, BC_INFLOW = 0, 1
+INFLOW_RECORD = 10                       # doubles per step of sl_set_inflow
 VEL_CONST, VEL_ROTATION, VEL_SWIRL, VEL_SINX = 0, 1, 2, 3
 C_BOUNDARY, C_MASS, C_ENERGY = 1, 2, 4
 FIT_HARD, FIT_SOFT = 0, 1
@@ -29,7 +30,7 @@ COUNTERS = ("elems", "solve_iters", "solve_floor", "solve_noconv", "energy_appli
 EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
            "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",
            "sl_integral_noalloc", "sl_batch_create", "sl_batch_step", "sl_batch_offset", "sl_counters",
-           "sl_timing", "sl_timing_read", "sl_last_error"]
+           "sl_timing", "sl_timing_read", "sl_set_inflow", "sl_last_error"]
 
 
 class SlMesh(C.Structure):
@@ -76,6 +77,7 @@ def load_library(path=LIB_PATH):
     lib.sl_sync.argtypes = [P, C.POINTER(C.c_uint32)]
     lib.sl_counters.argtypes = [P, C.POINTER(C.c_uint64)]
     lib.sl_timing.argtypes = [P, C.c_int]
+    lib.sl_set_inflow.argtypes = [P, P, C.c_int64]
     lib.sl_timing_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.sl_max_dt.argtypes = [P, C.POINTER(SlVelocity), C.c_int, C.POINTER(C.c_double)]
     lib.sl_state_size.argtypes = [P]
@@ -247,6 +249,19 @@ class Context:
         arr = (C.c_uint64 * len(COUNTERS))()
         self._check(self._lib.sl_counters(self._h, arr))
         return dict(zip(COUNTERS, (int(v) for v in arr)))
+
+    def set_inflow(self, values, step_stride=INFLOW_RECORD):
+        """Time-dependent inflow records (sl_set_inflow): a CUDA float64 tensor of records of
+        INFLOW_RECORD values per step (kept referenced here while set), or None."""
+        if values is None:
+            self._inflow = None
+            self._check(self._lib.sl_set_inflow(self._h, None, 0))
+            return
+        import torch
+        if not (values.is_cuda and values.dtype == torch.float64 and values.is_contiguous()):
+            raise ValueError("inflow records: a contiguous CUDA float64 tensor")
+        self._check(self._lib.sl_set_inflow(self._h, _ptr(values), int(step_stride)))
+        self._inflow = values
 
     def timing(self, enable):
         """Start (True) or end (False) a kernel-timing session (sl_timing)."""

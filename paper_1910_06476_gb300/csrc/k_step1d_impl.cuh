@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
       (void)dv;
       const double un = side ? u : -u;
       const double own = sm.tr[side][tid];
-      const double other = ghostface ? P.ghost : sm.tr[1 - side][nbt];
+      const double other = ghostface ? (P.gtab ? P.gtab[side * 5] : P.ghost) : sm.tr[1 - side][nbt];
       double val;
       if (un > TIE) val = own;
       else if (un < -TIE) val = other;
@@ -251,8 +251,9 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
           vel1d(P, xf, u, dv);
           const double un = side ? u : -u;
           if (un < -TIE) {
-            netm += c_rk_b[P.rk][s] * un * P.ghost;
-            nete += c_rk_b[P.rk][s] * un * P.ghost * P.ghost;
+            const double g = P.gtab ? P.gtab[side * 5 + 1 + s] : P.ghost;
+            netm += c_rk_b[P.rk][s] * un * g;
+            nete += c_rk_b[P.rk][s] * un * g * g;
           }
         }
       }

@@ -712,6 +712,7 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
   P.m = c->fit[lin][opt->fit == SL_FIT_SOFT].m;
   P.picard_rtol = opt->picard_rtol > 0.0 ? opt->picard_rtol : 1e-13;
   P.picard_cap = opt->picard_cap > 0 ? opt->picard_cap : 60;
+  P.gtab = c->inflow_step;
 
   const double* T = c->d_tables;
   const size_t* off = c->table_off[lin][opt->fit == SL_FIT_SOFT];
@@ -800,7 +801,18 @@ sl_status sl_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocit
     st = check_dt(c, c->mesh, vel, t, dt);
   }
   if (st != SL_OK) return st;
+  c->inflow_step = c->inflow;
   return step_dispatch(c, phi_in, phi_out, vel, t, dt, opt);
+}
+
+sl_status sl_set_inflow(sl_ctx* c, const double* values, int64_t step_stride) {
+  if (!c) return SL_EINVAL;
+  if (step_stride < 0) return fail(c, SL_EINVAL, "step_stride must be >= 0");
+  if (c->mesh.dim != 1 || c->precision != SL_FP64 || !c->geo_host.empty())
+    return fail(c, SL_EUNSUPPORTED, "inflow records are read by the 1D FP64 path");
+  c->inflow = values;
+  c->inflow_stride = values ? step_stride : 0;
+  return SL_OK;
 }
 
 sl_status sl_batch_step(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocity* vel, const double* t,
@@ -830,6 +842,8 @@ sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, do
     return st;
   }
   if (!std::isfinite(t0 + nsteps * dt)) return fail(c, SL_EINVAL, "t0 + nsteps dt must be finite");
+  if (c->inflow && nsteps > 1 && c->inflow_stride < SL_INFLOW_RECORD)
+    return fail(c, SL_EINVAL, "inflow records of a run need step_stride >= SL_INFLOW_RECORD");
   // operators that a step would upload are prepared before (and outside) the capture
   if (uses_m2c(c, vel, opt) && (st = ensure_m2c(c, vel, dt, opt)) != SL_OK) return st;
   if (!c->run_stream) {
@@ -840,7 +854,8 @@ sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, do
   }
   std::vector<double> key = {(double)vel->kind, t0, dt, (double)nsteps, (double)opt->constraints,
                              (double)opt->rk_order, (double)opt->fit, (double)opt->bvalue, opt->picard_rtol,
-                             (double)opt->picard_cap, (double)(uintptr_t)phi_a, (double)(uintptr_t)phi_b};
+                             (double)opt->picard_cap, (double)(uintptr_t)phi_a, (double)(uintptr_t)phi_b,
+                             (double)(uintptr_t)c->inflow, (double)c->inflow_stride};
   for (int i = 0; i < 6; ++i) key.push_back(vel->p[i]);
   if (!c->run_valid || key != c->run_key) {
     if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
@@ -880,6 +895,7 @@ sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, do
     void* b = phi_b;
     for (int s = 0; s < nsteps && st == SL_OK; ++s) {
       if (batch) c->geo_override = c->d_geo_run + (size_t)s * c->nprob;
+      c->inflow_step = c->inflow ? c->inflow + (int64_t)s * c->inflow_stride : nullptr;
       st = step_dispatch(c, a, b, vel, t0 + s * dt, dt, opt);
       std::swap(a, b);
     }
@@ -935,8 +951,13 @@ sl_status sl_run_host(sl_ctx* c, const double* host_in, double* host_out, const 
                                c->stream));
     launch_pack(c->nvals, plane_stride(c->nvals), c->d_io64, (float*)a, c->stream);
   }
+  if (c->inflow && nsteps > 1 && c->inflow_stride < SL_INFLOW_RECORD)
+    return fail(c, SL_EINVAL, "inflow records of a run need step_stride >= SL_INFLOW_RECORD");
+  const double* inflow0 = c->inflow;        // step s reads record s
   for (int s = 0; s < nsteps; ++s) {
+    c->inflow = inflow0 ? inflow0 + (int64_t)s * c->inflow_stride : nullptr;
     sl_status st = sl_step(c, a, b, vel, t0 + s * dt, dt, opt);
+    c->inflow = inflow0;
     if (st != SL_OK) return st;
     std::swap(a, b);
   }

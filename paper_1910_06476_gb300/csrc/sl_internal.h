@@ -82,6 +82,7 @@ struct StepParams {
   int m;                                 // active linear rows
   double picard_rtol;
   int picard_cap;
+  const double* gtab;                    // 1D inflow record of this step (sl_set_inflow), or null
 };
 
 void launch_step1d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in,
@@ -321,5 +322,10 @@ struct sl_ctx {
   std::vector<cudaEvent_t> tev;          // 3 per step, reused across timing sessions
   size_t tused = 0;                      // events of the current session
   std::vector<char> tdone;               // per timed step: its end event was recorded
+  // time-dependent inflow records (sl_set_inflow); inflow_step is the record of the step being
+  // enqueued
+  const double* inflow = nullptr;
+  int64_t inflow_stride = 0;
+  const double* inflow_step = nullptr;
   std::string err;
 };
