@@ -55,6 +55,9 @@ in the design notes):
       the minimum spacing between adjacent nodes.
   R10 p-nonconforming faces: the upwind neighbour's polynomial is evaluated at this element's
       face points; face fluxes use the Gauss rule of the side with more nodes.
+  R15 Nodal velocity (Sec. 4.2, a velocity given at the Gauss nodes by an Eulerian solver):
+      the containing element's Lagrange interpolant, linear in time over the step; on a face
+      the average of the elements sharing it; its divergence from the same interpolants.
 
 Parity pins (see tests/test_oracle_*.py): nodes/weights against numpy's leggauss and
 monomial exactness; basis cardinality and polynomial reproduction; exact translation of
@@ -75,7 +78,7 @@ import numpy as np
 import scipy.linalg
 
 GAUSS_LEGENDRE, CHEB_GAUSS = 0, 1
-VEL_CONST, VEL_ROTATION, VEL_SWIRL, VEL_SINX = 0, 1, 2, 3
+VEL_CONST, VEL_ROTATION, VEL_SWIRL, VEL_SINX, VEL_NODAL = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_INFLOW = 0, 1
 C_BOUNDARY, C_MASS, C_ENERGY = 1, 2, 4
 FIT_HARD, FIT_SOFT = 0, 1
@@ -132,6 +135,25 @@ def lagrange(nodes, x):
     return L
 
 
+def lagrange_deriv(nodes, x):
+    """Derivatives l_j'(x) of the Lagrange basis (product rule on the product formula):
+    l_j'(x) = sum_{k != j} 1/(x_j - x_k) prod_{m != j, k} (x - x_m)/(x_j - x_m)."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    n = nodes.size
+    D = np.zeros((x.size, n))
+    for j in range(n):
+        for k in range(n):
+            if k == j:
+                continue
+            term = np.full(x.size, 1.0 / (nodes[j] - nodes[k]))
+            for m in range(n):
+                if m != j and m != k:
+                    term *= (x - nodes[m]) / (nodes[j] - nodes[m])
+            D[:, j] += term
+    return D
+
+
 def interpolatory_weights(nodes):
     """w_j = integral_0^1 l_j(xi) d xi (reading R2), integrated exactly by a Gauss rule."""
     gx, gw = gauss_legendre_01(len(nodes) + 1)
@@ -155,6 +177,85 @@ def nodes_weights(n, basis):
 class Vel:
     kind: int
     p: tuple
+    nodal: object = None         # NodalField for VEL_NODAL
+
+
+@dataclass
+class NodalField:
+    """A velocity known at the solution nodes, as an Eulerian solver on the same elements would
+    provide it (Sec. 4.2: the particles start at the Gauss nodes, where that velocity is given;
+    between nodes it is interpolated).  u0, v0 are the node values at t0 and u1, v1 at t1, in the
+    state's shape ((K, n) in 1D, (ky, kx, n, n) in 2D; v unused in 1D).  Reading R15: at a point
+    the field is the Lagrange interpolant of the element that contains it (extrapolated from the
+    boundary element outside a non-periodic domain, wrapped across a periodic one), linear in
+    time between t0 and t1; on a face (within FACE_RTOL of it) it is the average over the
+    elements that share the face, so that both sides see one velocity there."""
+    setup: object
+    t0: float
+    t1: float
+    u0: np.ndarray
+    u1: np.ndarray
+    v0: np.ndarray = None
+    v1: np.ndarray = None
+
+
+FACE_RTOL = 1e-12           # a point this close to a face, relative to |x0| + |x1|, is on it (R15)
+
+
+def _nodal_locate(x, lo, hi, h, K, periodic):
+    """Elements (index, reference coordinate, weight) that give the nodal field at coordinate x
+    along one direction (R15): one element inside, the two sharing a face on it."""
+    s = (x - lo) / h
+    r = int(np.rint(s))
+    if abs(x - (lo + r * h)) <= FACE_RTOL * (abs(lo) + abs(hi)):
+        sides = []
+        for k, z in ((r - 1, 1.0), (r, 0.0)):
+            if 0 <= k < K:
+                sides.append((k, z))
+            elif periodic:
+                sides.append((k % K, z))
+        return [(k, z, 1.0 / len(sides)) for k, z in sides]
+    k = int(math.floor(s))
+    z = s - k
+    if periodic:
+        return [(k % K, z, 1.0)]
+    kc = min(max(k, 0), K - 1)
+    return [(kc, s - kc, 1.0)]
+
+
+def nodal_velocity(field, x, y, t):
+    """u, v and div u of a NodalField at physical points (reading R15)."""
+    st = field.setup
+    th = (t - field.t0) / (field.t1 - field.t0)
+    xi, _ = nodes_weights(st.n, st.basis)
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    y = np.zeros_like(x) if y is None else np.atleast_1d(np.asarray(y, dtype=np.float64))
+    U = (1.0 - th) * np.asarray(field.u0, dtype=np.float64) + th * np.asarray(field.u1, dtype=np.float64)
+    u = np.zeros_like(x)
+    v = np.zeros_like(x)
+    dv = np.zeros_like(x)
+    x0, x1 = st.box[0], st.box[1]
+    if st.dim == 1:
+        per = st.bc[0] == BC_PERIODIC
+        for q in range(x.size):
+            for k, z, wt in _nodal_locate(x[q], x0, x1, st.hx, st.kx, per):
+                u[q] += wt * (lagrange(xi, [z])[0] @ U[k])
+                dv[q] += wt * (lagrange_deriv(xi, [z])[0] @ U[k]) / st.hx
+        return u, v, dv
+    V = (1.0 - th) * np.asarray(field.v0, dtype=np.float64) + th * np.asarray(field.v1, dtype=np.float64)
+    y0, y1 = st.box[2], st.box[3]
+    perx, pery = st.bc[0] == BC_PERIODIC, st.bc[2] == BC_PERIODIC
+    for q in range(x.size):
+        for kx_, zx, wx in _nodal_locate(x[q], x0, x1, st.hx, st.kx, perx):
+            for ky_, zy, wy in _nodal_locate(y[q], y0, y1, st.hy, st.ky, pery):
+                Lx, Ly = lagrange(xi, [zx])[0], lagrange(xi, [zy])[0]
+                Dx, Dy = lagrange_deriv(xi, [zx])[0], lagrange_deriv(xi, [zy])[0]
+                Ue, Ve = U[ky_, kx_], V[ky_, kx_]          # [j (y), i (x)]
+                wt = wx * wy
+                u[q] += wt * (Ly @ Ue @ Lx)
+                v[q] += wt * (Ly @ Ve @ Lx)
+                dv[q] += wt * ((Ly @ Ue @ Dx) / st.hx + (Dy @ Ve @ Lx) / st.hy)
+    return u, v, dv
 
 
 def velocity(vel, x, y, t):
@@ -178,6 +279,8 @@ def velocity(vel, x, y, t):
         return u, v, z                                 # divergence-free
     if vel.kind == VEL_SINX:
         return -np.sin(x), z, -np.cos(x)
+    if vel.kind == VEL_NODAL:
+        return nodal_velocity(vel.nodal, x, y, t)
     raise ValueError("unknown velocity kind")
 
 
@@ -195,6 +298,11 @@ def max_speed(vel, box):
         return 1.0, 1.0
     if vel.kind == VEL_SINX:
         return 1.0, 0.0
+    if vel.kind == VEL_NODAL:       # the node values bound the speed (R15)
+        f = vel.nodal
+        um = max(np.max(np.abs(f.u0)), np.max(np.abs(f.u1)))
+        vm = 0.0 if f.v0 is None else max(np.max(np.abs(f.v0)), np.max(np.abs(f.v1)))
+        return float(um), float(vm)
     raise ValueError
 
 
