@@ -80,8 +80,25 @@ enum { SL_BC_PERIODIC = 0, SL_BC_INFLOW = 1 };
  *   SL_VEL_ROTATION p = {omega, cx, cy}: u = -omega (y - cy), v = omega (x - cx)
  *   SL_VEL_SWIRL    p = {T}: u = sin^2(pi x) sin(2 pi y) cos(pi t / T),
  *                            v = -sin^2(pi y) sin(2 pi x) cos(pi t / T)
- *   SL_VEL_SINX     u = -sin x, 1D only (Sec. 5.2, eq. usin_lagr) */
-enum { SL_VEL_CONST = 0, SL_VEL_ROTATION = 1, SL_VEL_SWIRL = 2, SL_VEL_SINX = 3 };
+ *   SL_VEL_SINX     u = -sin x, 1D only (Sec. 5.2, eq. usin_lagr)
+ *   SL_VEL_NODAL    a velocity given at the solution nodes, as an Eulerian solver on the same
+ *                   elements provides it (Sec. 4.2: the particles start at the Gauss nodes, where
+ *                   that velocity is known).  nodal points to DEVICE doubles laid out
+ *                   [2][dim][state values]: the u (then, in 2D, v) node values at t and at t + dt
+ *                   of the step, each in the context's state layout.  Between nodes the field is
+ *                   the Lagrange interpolant of the element that contains the point (extrapolated
+ *                   from the boundary element beyond a non-periodic face, wrapped across a
+ *                   periodic one), linear in time over the step; on a face (within 1e-12 of
+ *                   |x0| + |x1|, resp. |y0| + |y1|) it is the average over the elements sharing
+ *                   it, so both sides see one velocity; div u comes from the same interpolants
+ *                   and enters the value equation (eq. 4.8).  p = {umax, vmax}: bounds of |u| and
+ *                   |v| that the caller supplies for sl_max_dt and the CFL check (the library
+ *                   does not read the device array on the host).  Step k of sl_run reads the
+ *                   array at nodal + k * nodal_step doubles (0: the same field every step).
+ *                   FP64 contexts with one node count (no batch); other contexts return
+ *                   SL_EUNSUPPORTED.  The caller keeps the array alive and unchanged while steps
+ *                   that read it are in flight. */
+enum { SL_VEL_CONST = 0, SL_VEL_ROTATION = 1, SL_VEL_SWIRL = 2, SL_VEL_SINX = 3, SL_VEL_NODAL = 4 };
 
 /* Constraint rows of the least-squares fit (eq. matrix_a). */
 enum { SL_C_BOUNDARY = 1, SL_C_MASS = 2, SL_C_ENERGY = 4 };
@@ -123,6 +140,8 @@ typedef struct {
 typedef struct {
   int kind;              /* SL_VEL_*                                                        */
   double p[6];           /* parameters, see SL_VEL_*                                        */
+  const double* nodal;   /* SL_VEL_NODAL: device node velocities (else ignored, may be NULL) */
+  int64_t nodal_step;    /* SL_VEL_NODAL: doubles between the arrays of successive sl_run steps */
 } sl_velocity;
 
 typedef struct {

@@ -18,7 +18,7 @@ GAUSS_LEGENDRE, CHEB_GAUSS = 0, 1
 FP64, MIXED = 0, 1
 BC_PERIODIC, BC_INFLOW = 0, 1
 INFLOW_RECORD = 10                       # doubles per step of sl_set_inflow
-VEL_CONST, VEL_ROTATION, VEL_SWIRL, VEL_SINX = 0, 1, 2, 3
+VEL_CONST, VEL_ROTATION, VEL_SWIRL, VEL_SINX, VEL_NODAL = 0, 1, 2, 3, 4
 C_BOUNDARY, C_MASS, C_ENERGY = 1, 2, 4
 FIT_HARD, FIT_SOFT = 0, 1
 BV_INTERP, BV_BACKTRACK = 0, 1
@@ -40,7 +40,7 @@ class SlMesh(C.Structure):
 
 
 class SlVelocity(C.Structure):
-    _fields_ = [("kind", C.c_int), ("p", C.c_double * 6)]
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 6), ("nodal", C.c_void_p), ("nodal_step", C.c_int64)]
 
 
 class SlOptions(C.Structure):
@@ -112,6 +112,20 @@ def velocity(kind, *p):
     v.kind = int(kind)
     for i, x in enumerate(p[:6]):
         v.p[i] = float(x)
+    return v
+
+
+def nodal_velocity(values, umax, vmax=0.0, step=0):
+    """SL_VEL_NODAL from a contiguous CUDA float64 tensor of node velocities laid out
+    [2][dim][state values] (u, v at t and at t + dt); umax, vmax bound |u|, |v|.  The returned
+    structure keeps the tensor referenced."""
+    import torch
+    if not (values.is_cuda and values.dtype == torch.float64 and values.is_contiguous()):
+        raise ValueError("nodal velocity: a contiguous CUDA float64 tensor")
+    v = velocity(VEL_NODAL, umax, vmax)
+    v.nodal = values.data_ptr()
+    v.nodal_step = int(step)
+    v._keep = values
     return v
 
 

@@ -30,53 +30,6 @@ static __constant__ double c_rk_b[5][4] = {
     {}, {1.0}, {0.5, 0.5}, {1.0 / 6, 2.0 / 3, 1.0 / 6}, {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}};
 static __constant__ double c_rk_c[5][4] = {{}, {0.0}, {0.0, 1.0}, {0.0, 0.5, 1.0}, {0.0, 0.5, 0.5, 1.0}};
 
-// velocity u(x, t) and its divergence in 1D (Sec. 5.1: constant; Sec. 5.2: u = -sin x)
-__device__ __forceinline__ void vel1d(const StepParams& P, double x, double& u, double& dv) {
-  if (P.vel_kind == SL_VEL_SINX) {
-    double s, c;
-    sincos(x, &s, &c);
-    u = -s;
-    dv = -c;
-  } else {
-    u = P.vp[0];
-    dv = 0.0;
-  }
-}
-
-// one explicit RK step of dx/dt = u, dphi/dt = -phi div u, size h (h < 0 runs backward)
-__device__ __forceinline__ void rk_step(const StepParams& P, double& x, double& ph, double t, double h) {
-  if (P.vel_kind == SL_VEL_CONST) {       // exact for any scheme: sum b = 1
-    x += h * P.vp[0];
-    return;
-  }
-  const int S = c_rk_s[P.rk];
-  double kx[4], kp[4];
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (s < S) {
-      double xs = x, ps = ph;
-#pragma unroll
-      for (int j = 0; j < s; ++j) {
-        xs += h * c_rk_a[P.rk][s][j] * kx[j];
-        ps += h * c_rk_a[P.rk][s][j] * kp[j];
-      }
-      double u, dv;
-      vel1d(P, xs, u, dv);
-      kx[s] = u;
-      kp[s] = -ps * dv;
-    }
-  }
-  double sx = 0.0, sp = 0.0;
-#pragma unroll
-  for (int s = 0; s < 4; ++s)
-    if (s < S) {
-      sx += c_rk_b[P.rk][s] * kx[s];
-      sp += c_rk_b[P.rk][s] * kp[s];
-    }
-  x += h * sx;
-  ph += h * sp;
-}
-
 // value at reference point z of the polynomial with nodal values v on nodes xn (barycentric
 // weights lam): sum_j lam_j prod_{m != j} (z - xn_m) v_j, by prefix/suffix products
 template <int NN>
@@ -94,6 +47,157 @@ __device__ __forceinline__ double eval_poly(const double* xn, const double* lam,
     suf *= d[j];
   }
   return out;
+}
+
+// the same polynomial and its derivative in z: the prefix and suffix products carry their
+// derivatives along (product rule), so nodes need no special case
+template <int NN>
+__device__ __forceinline__ void eval_poly_d(const double* xn, const double* lam, const double* v, double z,
+                                            double& val, double& der) {
+  double d[NN], pre[NN], dpre[NN];
+#pragma unroll
+  for (int m = 0; m < NN; ++m) d[m] = z - xn[m];
+  double acc = 1.0, dacc = 0.0;
+#pragma unroll
+  for (int m = 0; m < NN; ++m) {
+    pre[m] = acc;
+    dpre[m] = dacc;
+    dacc = dacc * d[m] + acc;
+    acc *= d[m];
+  }
+  double suf = 1.0, dsuf = 0.0, out = 0.0, dout = 0.0;
+#pragma unroll
+  for (int j = NN - 1; j >= 0; --j) {
+    const double c = lam[j] * v[j];
+    out += c * pre[j] * suf;
+    dout += c * (dpre[j] * suf + pre[j] * dsuf);
+    dsuf = dsuf * d[j] + suf;
+    suf *= d[j];
+  }
+  val = out;
+  der = dout;
+}
+
+// SL_VEL_NODAL in 1D: the node velocities of element k at time t (linear between the step's
+// two arrays), evaluated with their derivative at reference point z
+template <int NN>
+__device__ __forceinline__ void nodal_elem1d(const StepParams& P, const double* xi, const double* lam, int k,
+                                             double z, double th, double& u, double& du) {
+  const double* U0 = P.nodal + (size_t)k * NN;
+  const double* U1 = U0 + P.nvals;
+  double v[NN];
+#pragma unroll
+  for (int j = 0; j < NN; ++j) v[j] = (1.0 - th) * U0[j] + th * U1[j];
+  eval_poly_d<NN>(xi, lam, v, z, u, du);
+}
+
+// the nodal field at physical x: the containing element's interpolant (the boundary element's
+// beyond a non-periodic face, wrapped across a periodic one); on a face the average over the
+// elements that share it
+template <int NN>
+__device__ void nodal1d(const StepParams& P, const double* xi, const double* lam, double x, double t, double& u,
+                        double& dv) {
+  const double h = P.hx, x1 = P.x0 + P.K * h;
+  const double th = (t - P.t) / P.dt;
+  const double s = (x - P.x0) / h;
+  const double r = rint(s);
+  const bool perW = P.bc[0] == SL_BC_PERIODIC, perE = P.bc[1] == SL_BC_PERIODIC;
+  u = 0.0;
+  dv = 0.0;
+  if (fabs(x - (P.x0 + r * h)) <= FACE_RTOL * (fabs(P.x0) + fabs(x1))) {
+    int ks[2];
+    double zs[2];
+    int cnt = 0;
+    const long long ri = (long long)r;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      long long k = side ? ri : ri - 1;
+      if (k < 0 || k >= P.K) {
+        if (!(k < 0 ? perW : perE)) continue;
+        k %= P.K;
+        if (k < 0) k += P.K;
+      }
+      ks[cnt] = (int)k;
+      zs[cnt] = side ? 0.0 : 1.0;
+      ++cnt;
+    }
+    for (int q = 0; q < cnt; ++q) {
+      double uq, dq;
+      nodal_elem1d<NN>(P, xi, lam, ks[q], zs[q], th, uq, dq);
+      u += uq / cnt;
+      dv += dq / h / cnt;
+    }
+    return;
+  }
+  const double fk = floor(s);
+  long long k = (long long)fk;
+  double z = s - fk;
+  if (k < 0 || k >= P.K) {
+    if (k < 0 ? perW : perE) {
+      k %= P.K;
+      if (k < 0) k += P.K;
+    } else {
+      k = k < 0 ? 0 : P.K - 1;
+      z = s - (double)k;
+    }
+  }
+  double du;
+  nodal_elem1d<NN>(P, xi, lam, (int)k, z, th, u, du);
+  dv = du / h;
+}
+
+// velocity u(x, t) and its divergence in 1D (Sec. 5.1: constant; Sec. 5.2: u = -sin x; Sec. 4.2:
+// given at the nodes)
+template <int NN>
+__device__ __forceinline__ void vel1d(const StepParams& P, const double* xi, const double* lam, double x, double t,
+                                      double& u, double& dv) {
+  if (P.vel_kind == SL_VEL_SINX) {
+    double s, c;
+    sincos(x, &s, &c);
+    u = -s;
+    dv = -c;
+  } else if (P.vel_kind == SL_VEL_NODAL) {
+    nodal1d<NN>(P, xi, lam, x, t, u, dv);
+  } else {
+    u = P.vp[0];
+    dv = 0.0;
+  }
+}
+
+// one explicit RK step of dx/dt = u, dphi/dt = -phi div u, size h (h < 0 runs backward)
+template <int NN>
+__device__ __forceinline__ void rk_step(const StepParams& P, const double* xi, const double* lam, double& x,
+                                        double& ph, double t, double h) {
+  if (P.vel_kind == SL_VEL_CONST) {       // exact for any scheme: sum b = 1
+    x += h * P.vp[0];
+    return;
+  }
+  const int S = c_rk_s[P.rk];
+  double kx[4], kp[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s < S) {
+      double xs = x, ps = ph;
+#pragma unroll
+      for (int j = 0; j < s; ++j) {
+        xs += h * c_rk_a[P.rk][s][j] * kx[j];
+        ps += h * c_rk_a[P.rk][s][j] * kp[j];
+      }
+      double u, dv;
+      vel1d<NN>(P, xi, lam, xs, t + c_rk_c[P.rk][s] * h, u, dv);
+      kx[s] = u;
+      kp[s] = -ps * dv;
+    }
+  }
+  double sx = 0.0, sp = 0.0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (s < S) {
+      sx += c_rk_b[P.rk][s] * kx[s];
+      sp += c_rk_b[P.rk][s] * kp[s];
+    }
+  x += h * sx;
+  ph += h * sp;
 }
 
 struct Smem1D {
@@ -151,7 +255,7 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
 #pragma unroll
     for (int i = 0; i < NN; ++i) {
       double x = xk + h * sm.xi[i], p = phi[i];
-      rk_step(P, x, p, P.t, P.dt);
+      rk_step<NN>(P, sm.xi, sm.lam, x, p, P.t, P.dt);
       xs[i] = (x - xk) / h;
       ps[i] = p;
     }
@@ -171,8 +275,8 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
     double T0, T1;
     if (P.bvalue == SL_BV_BACKTRACK) {
       double f0 = xk, f1 = xk + h, g0 = 1.0, g1 = 1.0;
-      rk_step(P, f0, g0, tn1, -P.dt);
-      rk_step(P, f1, g1, tn1, -P.dt);
+      rk_step<NN>(P, sm.xi, sm.lam, f0, g0, tn1, -P.dt);
+      rk_step<NN>(P, sm.xi, sm.lam, f1, g1, tn1, -P.dt);
       T0 = eval_poly<NN>(sm.xi, sm.lam, phi, (f0 - xk) / h) / g0;
       T1 = eval_poly<NN>(sm.xi, sm.lam, phi, (f1 - xk) / h) / g1;
     } else {
@@ -191,11 +295,11 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
         for (int side = 0; side < 2; ++side) {
           const double xf = xk + (side ? h : 0.0);
           double u, dv;
-          vel1d(P, xf, u, dv);
+          vel1d<NN>(P, sm.xi, sm.lam, xf, tau, u, dv);
           const double un = side ? u : -u;
           if (un > TIE) {
             double fx = xf, g = 1.0;
-            if (cs != 0.0) rk_step(P, fx, g, tau, -cs * P.dt);
+            if (cs != 0.0) rk_step<NN>(P, sm.xi, sm.lam, fx, g, tau, -cs * P.dt);
             const double val = eval_poly<NN>(sm.xi, sm.lam, phi, (fx - xk) / h) / g;
             if (side) { fm1 += bs * un * val; fe1 += bs * un * val * val; }
             else { fm0 += bs * un * val; fe0 += bs * un * val * val; }
@@ -225,7 +329,7 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
     const int nbt = side ? tid + 1 : tid - 1;     // neighbour's thread in this CTA
     if (P.cons & SL_C_BOUNDARY) {
       double u, dv;
-      vel1d(P, xf, u, dv);
+      vel1d<NN>(P, sm.xi, sm.lam, xf, tn1, u, dv);
       (void)dv;
       const double un = side ? u : -u;
       const double own = sm.tr[side][tid];
@@ -247,8 +351,7 @@ __global__ void __launch_bounds__(BLOCK) k_step1d_f64(StepParams P, Tables1D tb,
         for (int s = 0; s < S; ++s) {
           const double tau = P.t + c_rk_c[P.rk][s] * P.dt;
           double u, dv;
-          (void)tau;
-          vel1d(P, xf, u, dv);
+          vel1d<NN>(P, sm.xi, sm.lam, xf, tau, u, dv);
           const double un = side ? u : -u;
           if (un < -TIE) {
             const double g = P.gtab ? P.gtab[side * 5 + 1 + s] : P.ghost;

@@ -58,38 +58,6 @@ __device__ __forceinline__ void vel2d(const StepParams& P, double x, double y, d
   }
 }
 
-// one explicit RK step of dx/dt = u, dy/dt = v of size h (h < 0 runs the characteristic back)
-__device__ __forceinline__ void rk2d(const StepParams& P, double& x, double& y, double t, double h) {
-  if (P.vel_kind == SL_VEL_CONST) {
-    x += h * P.vp[0];
-    y += h * P.vp[1];
-    return;
-  }
-  const int S = c_rk_s[P.rk];
-  double kx[4], ky[4];
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (s < S) {
-      double xs = x, ys = y;
-#pragma unroll
-      for (int j = 0; j < s; ++j) {
-        xs += h * c_rk_a[P.rk][s][j] * kx[j];
-        ys += h * c_rk_a[P.rk][s][j] * ky[j];
-      }
-      vel2d(P, xs, ys, t + c_rk_c[P.rk][s] * h, kx[s], ky[s]);
-    }
-  }
-  double sx = 0.0, sy = 0.0;
-#pragma unroll
-  for (int s = 0; s < 4; ++s)
-    if (s < S) {
-      sx += c_rk_b[P.rk][s] * kx[s];
-      sy += c_rk_b[P.rk][s] * ky[s];
-    }
-  x += h * sx;
-  y += h * sy;
-}
-
 // Lagrange basis on the fixed nodes at z: out_l = lam_l prod_{k != l} (z - xi_k)
 template <int NN>
 __device__ __forceinline__ void basis_at(const double* xi, const double* lam, double z, double* out) {
@@ -105,6 +73,169 @@ __device__ __forceinline__ void basis_at(const double* xi, const double* lam, do
     out[l] = lam[l] * pre[l] * suf;
     suf *= d[l];
   }
+}
+
+// Lagrange basis and its derivative at z (prefix and suffix products carry their derivatives)
+template <int NN>
+__device__ __forceinline__ void basis_d(const double* xi, const double* lam, double z, double* L, double* D) {
+  double d[NN], pre[NN], dpre[NN];
+#pragma unroll
+  for (int k = 0; k < NN; ++k) d[k] = z - xi[k];
+  double acc = 1.0, dacc = 0.0;
+#pragma unroll
+  for (int k = 0; k < NN; ++k) {
+    pre[k] = acc;
+    dpre[k] = dacc;
+    dacc = dacc * d[k] + acc;
+    acc *= d[k];
+  }
+  double suf = 1.0, dsuf = 0.0;
+#pragma unroll
+  for (int l = NN - 1; l >= 0; --l) {
+    L[l] = lam[l] * pre[l] * suf;
+    D[l] = lam[l] * (dpre[l] * suf + pre[l] * dsuf);
+    dsuf = dsuf * d[l] + suf;
+    suf *= d[l];
+  }
+}
+
+// SL_VEL_NODAL along one direction: the elements (index, reference coordinate) that give the field
+// at coordinate x, two when x lies on a face (the elements sharing it), else the containing one
+// (the boundary element beyond a non-periodic face, wrapped across a periodic one); returns the count
+__device__ __forceinline__ int nodal_locate(double x, double lo, double h, int K, bool per, int* ks, double* zs) {
+  const double hi = lo + K * h;
+  const double s = (x - lo) / h;
+  const double r = rint(s);
+  if (fabs(x - (lo + r * h)) <= FACE_RTOL * (fabs(lo) + fabs(hi))) {
+    const long long ri = (long long)r;
+    int cnt = 0;
+    for (int side = 0; side < 2; ++side) {
+      long long k = side ? ri : ri - 1;
+      if (k < 0 || k >= K) {
+        if (!per) continue;
+        k %= K;
+        if (k < 0) k += K;
+      }
+      ks[cnt] = (int)k;
+      zs[cnt] = side ? 0.0 : 1.0;
+      ++cnt;
+    }
+    return cnt;
+  }
+  const double fk = floor(s);
+  long long k = (long long)fk;
+  double z = s - fk;
+  if (k < 0 || k >= K) {
+    if (per) {
+      k %= K;
+      if (k < 0) k += K;
+    } else {
+      k = k < 0 ? 0 : K - 1;
+      z = s - (double)k;
+    }
+  }
+  ks[0] = (int)k;
+  zs[0] = z;
+  return 1;
+}
+
+// SL_VEL_NODAL: u, v and div u at (x, y, t) from the node velocities of the step (linear in time),
+// averaged over the elements that share a face or corner the point lies on
+template <int NN>
+__device__ __noinline__ void nodal2d(const StepParams& P, const double* xi, const double* lam, double x, double y,
+                                     double t, double& u, double& v, double& dv) {
+  constexpr int ND = NN * NN;
+  const double th = (t - P.t) / P.dt;
+  int kxs[2], kys[2];
+  double zxs[2], zys[2];
+  const int nx = nodal_locate(x, P.x0, P.hx, P.kx, P.bc[0] == SL_BC_PERIODIC, kxs, zxs);
+  const int ny = nodal_locate(y, P.y0, P.hy, P.ky, P.bc[2] == SL_BC_PERIODIC, kys, zys);
+  const double wt = 1.0 / (nx * ny);
+  u = v = dv = 0.0;
+  for (int a = 0; a < ny; ++a) {
+    double Ly[NN], Dy[NN];
+    basis_d<NN>(xi, lam, zys[a], Ly, Dy);
+    for (int b = 0; b < nx; ++b) {
+      double Lx[NN], Dx[NN];
+      basis_d<NN>(xi, lam, zxs[b], Lx, Dx);
+      const double* U0 = P.nodal + ((size_t)kys[a] * P.kx + kxs[b]) * ND;
+      const double* V0 = U0 + P.nvals;
+      const double* U1 = U0 + 2 * P.nvals;
+      const double* V1 = U0 + 3 * P.nvals;
+      double su = 0.0, sv = 0.0, sux = 0.0, svy = 0.0;
+      for (int m = 0; m < NN; ++m) {
+        double ru = 0.0, rv = 0.0, rux = 0.0;
+#pragma unroll
+        for (int l = 0; l < NN; ++l) {
+          const double uu = (1.0 - th) * U0[m * NN + l] + th * U1[m * NN + l];
+          const double vv = (1.0 - th) * V0[m * NN + l] + th * V1[m * NN + l];
+          ru += Lx[l] * uu;
+          rv += Lx[l] * vv;
+          rux += Dx[l] * uu;
+        }
+        su += Ly[m] * ru;
+        sv += Ly[m] * rv;
+        sux += Ly[m] * rux;
+        svy += Dy[m] * rv;
+      }
+      u += wt * su;
+      v += wt * sv;
+      dv += wt * (sux / P.hx + svy / P.hy);
+    }
+  }
+}
+
+// velocity and its divergence (zero for the analytic kinds, which are divergence free); NOD: the
+// kernel is the instantiation that reads nodal velocities (the others carry no nodal code)
+template <int NN, bool NOD>
+__device__ __forceinline__ void vel2dd(const StepParams& P, const double* xi, const double* lam, double x, double y,
+                                       double t, double& u, double& v, double& dv) {
+  if (NOD) {
+    nodal2d<NN>(P, xi, lam, x, y, t, u, v, dv);
+  } else {
+    vel2d(P, x, y, t, u, v);
+    dv = 0.0;
+  }
+}
+
+// one explicit RK step of dx/dt = u, dy/dt = v and of the value factor dg/dt = -g div u (eq. 4.8;
+// g stays 1 for divergence-free kinds), size h (h < 0 runs the characteristic back)
+template <int NN, bool NOD>
+__device__ __forceinline__ void rk2d(const StepParams& P, const double* xi, const double* lam, double& x, double& y,
+                                     double& g, double t, double h) {
+  if (P.vel_kind == SL_VEL_CONST) {
+    x += h * P.vp[0];
+    y += h * P.vp[1];
+    return;
+  }
+  const int S = c_rk_s[P.rk];
+  double kx[4], ky[4], kg[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s < S) {
+      double xs = x, ys = y, gs = g;
+#pragma unroll
+      for (int j = 0; j < s; ++j) {
+        xs += h * c_rk_a[P.rk][s][j] * kx[j];
+        ys += h * c_rk_a[P.rk][s][j] * ky[j];
+        gs += h * c_rk_a[P.rk][s][j] * kg[j];
+      }
+      double dv;
+      vel2dd<NN, NOD>(P, xi, lam, xs, ys, t + c_rk_c[P.rk][s] * h, kx[s], ky[s], dv);
+      kg[s] = -gs * dv;
+    }
+  }
+  double sx = 0.0, sy = 0.0, sg = 0.0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (s < S) {
+      sx += c_rk_b[P.rk][s] * kx[s];
+      sy += c_rk_b[P.rk][s] * ky[s];
+      sg += c_rk_b[P.rk][s] * kg[s];
+    }
+  x += h * sx;
+  y += h * sy;
+  if (NOD) g += h * sg;
 }
 
 // deterministic block reductions (fixed tree order); every thread gets the result
@@ -154,7 +285,7 @@ __device__ __forceinline__ int nb_index(const StepParams& P, int ex, int ey, int
   return jy * P.kx + jx;
 }
 
-template <int NN>
+template <int NN, bool NOD>
 __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb, Map2D M,
                                                      const double* __restrict__ in, Work2D W, unsigned* status) {
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
@@ -183,11 +314,12 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb
   double Lx[NN], Ly[NN], phs = 0.0, dxs = 0.0, dys = 0.0;
   if (part) {
     double x = x0 + hx * s_xi[i], y = y0 + hy * s_xi[j];
-    rk2d(P, x, y, P.t, P.dt);
+    double g = 1.0;                          // value factor of eq. 4.8 (1 when div u = 0)
+    rk2d<NN, NOD>(P, s_xi, s_lam, x, y, g, P.t, P.dt);
     const double xs = (x - x0) / hx, ys = (y - y0) / hy;
     basis_at<NN>(s_xi, s_lam, xs, Lx);
     basis_at<NN>(s_xi, s_lam, ys, Ly);
-    phs = s_phi[tid];                       // divergence-free velocity: phi* = phi^n
+    phs = NOD ? s_phi[tid] * g : s_phi[tid];
     dxs = xs - s_xi[i];
     dys = ys - s_xi[j];
   }
@@ -256,7 +388,8 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb
     if (P.bvalue == SL_BV_BACKTRACK) {
       double fx = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
       double fy = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
-      rk2d(P, fx, fy, P.t + P.dt, -P.dt);
+      double gf = 1.0;
+      rk2d<NN, NOD>(P, s_xi, s_lam, fx, fy, gf, P.t + P.dt, -P.dt);
       double bx[NN], by[NN];
       basis_at<NN>(s_xi, s_lam, (fx - x0) / hx, bx);
       basis_at<NN>(s_xi, s_lam, (fy - y0) / hy, by);
@@ -267,6 +400,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb
         for (int l = 0; l < NN; ++l) row += s_phi[mm * NN + l] * bx[l];
         acc += by[mm] * row;
       }
+      if (NOD) acc /= gf;
     } else {
       const double* L = (f == 1 || f == 3) ? s_l1 : s_l0;
 #pragma unroll
@@ -298,12 +432,12 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb
       for (int s = 0; s < S; ++s) {
         const double cs = c_rk_c[P.rk][s];
         const double tau = P.t + cs * P.dt;
-        double u, v;
-        vel2d(P, xf, yf, tau, u, v);
+        double u, v, dvf;
+        vel2dd<NN, NOD>(P, s_xi, s_lam, xf, yf, tau, u, v, dvf);
         const double un = u * nx + v * ny;
         if (un > TIE) {
-          double fx = xf, fy = yf;
-          if (cs != 0.0) rk2d(P, fx, fy, tau, -cs * P.dt);
+          double fx = xf, fy = yf, gf = 1.0;
+          if (cs != 0.0) rk2d<NN, NOD>(P, s_xi, s_lam, fx, fy, gf, tau, -cs * P.dt);
           double bx[NN], by[NN];
           basis_at<NN>(s_xi, s_lam, (fx - x0) / hx, bx);
           basis_at<NN>(s_xi, s_lam, (fy - y0) / hy, by);
@@ -315,6 +449,7 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb
             for (int l = 0; l < NN; ++l) row += s_phi[mm * NN + l] * bx[l];
             val += by[mm] * row;
           }
+          if (NOD) val /= gf;
           const double bw = c_rk_b[P.rk][s] * Wq * un;
           fm += bw * val;
           fe += bw * val * val;
@@ -333,13 +468,13 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb
   }
 }
 
-template <int NN>
+template <int NN, bool NOD>
 __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, Tables1D tb, Map2D M,
                                                      const double* __restrict__ in, Work2D W, double* __restrict__ out,
                                                      unsigned* status) {
   constexpr int ND = Shape<NN>::ND, NT = Shape<NN>::NT;
   constexpr int MMAX = 4 * NN + 1;
-  __shared__ double s_xi[NN], s_w[NN], s_l0[NN], s_l1[NN];
+  __shared__ double s_xi[NN], s_lam[NN], s_w[NN], s_l0[NN], s_l1[NN];
   __shared__ double s_ph[ND], s_a[ND];
   __shared__ double s_r[MMAX], s_d[MMAX], s_ca[MMAX];
   __shared__ double s_red[NT / 32];
@@ -350,7 +485,10 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, Tables1D tb
   const double hx = P.hx, hy = P.hy;
   const double x0 = P.x0 + ex * hx, y0 = P.y0 + ey * hy;
   const double tn1 = P.t + P.dt;
-  if (tid < NN) { s_xi[tid] = tb.xi[tid]; s_w[tid] = tb.w[tid]; s_l0[tid] = tb.l0[tid]; s_l1[tid] = tb.l1[tid]; }
+  if (tid < NN) {
+    s_xi[tid] = tb.xi[tid]; s_lam[tid] = tb.lam[tid]; s_w[tid] = tb.w[tid];
+    s_l0[tid] = tb.l0[tid]; s_l1[tid] = tb.l1[tid];
+  }
   const bool part = tid < ND;
   const int i = tid % NN, j = tid / NN;
   double phn = 0.0, ph = 0.0;
@@ -378,8 +516,8 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, Tables1D tb
     }
     const double xf = f == 0 ? x0 : f == 1 ? x0 + hx : x0 + hx * s_xi[q];
     const double yf = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
-    double u, v;
-    vel2d(P, xf, yf, tn1, u, v);
+    double u, v, dvf;
+    vel2dd<NN, NOD>(P, s_xi, s_lam, xf, yf, tn1, u, v, dvf);
     const double un = f == 0 ? -u : f == 1 ? u : f == 2 ? -v : v;
     double val;
     if (un > TIE) val = own;
@@ -417,8 +555,8 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p2(StepParams P0, Tables1D tb
             const double yf = f == 2 ? y0 : f == 3 ? y0 + hy : y0 + hy * s_xi[q];
             const double Wq = (f < 2 ? hy : hx) * s_w[q];
             for (int s = 0; s < c_rk_s[P.rk]; ++s) {
-              double u, v;
-              vel2d(P, xf, yf, P.t + c_rk_c[P.rk][s] * P.dt, u, v);
+              double u, v, dvf;
+              vel2dd<NN, NOD>(P, s_xi, s_lam, xf, yf, P.t + c_rk_c[P.rk][s] * P.dt, u, v, dvf);
               const double un = f == 0 ? -u : f == 1 ? u : f == 2 ? -v : v;
               if (un < -TIE) {
                 netm += c_rk_b[P.rk][s] * Wq * un * P.ghost;
@@ -546,8 +684,14 @@ template <int NN>
 void launch_n(int phase, const StepParams& p, const Tables1D& tb, const Map2D& m, int64_t count, const double* in,
               double* out, const Work2D& w, unsigned* st, cudaStream_t s) {
   if (count <= 0) return;
-  if (phase == 1) k_p1<NN><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, tb, m, in, w, st);
-  else k_p2<NN><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, tb, m, in, w, out, st);
+  const bool nod = p.vel_kind == SL_VEL_NODAL;
+  if (phase == 1) {
+    if (nod) k_p1<NN, true><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, tb, m, in, w, st);
+    else k_p1<NN, false><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, tb, m, in, w, st);
+  } else {
+    if (nod) k_p2<NN, true><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, tb, m, in, w, out, st);
+    else k_p2<NN, false><<<(unsigned)count, Shape<NN>::NT, 0, s>>>(p, tb, m, in, w, out, st);
+  }
 }
 
 }  // namespace k2d

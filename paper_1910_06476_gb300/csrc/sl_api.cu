@@ -48,13 +48,17 @@ void max_speed(const sl_mesh& M, const sl_velocity* v, double& um, double& vm) {
     }
     case SL_VEL_SWIRL: um = vm = 1.0; break;
     case SL_VEL_SINX: um = 1.0; vm = 0.0; break;
+    case SL_VEL_NODAL: um = v->p[0]; vm = M.dim == 2 ? v->p[1] : 0.0; break;
     default: break;
   }
 }
 
 bool valid_velocity(const sl_ctx* c, const sl_velocity* v) {
   if (!v) return false;
-  if (v->kind < SL_VEL_CONST || v->kind > SL_VEL_SINX) return false;
+  if (v->kind < SL_VEL_CONST || v->kind > SL_VEL_NODAL) return false;
+  if (v->kind == SL_VEL_NODAL &&
+      (!v->nodal || ((uintptr_t)v->nodal & 7u) || v->nodal_step < 0 || !(v->p[0] >= 0.0) || !(v->p[1] >= 0.0)))
+    return false;
   if (c->mesh.dim == 1 && (v->kind == SL_VEL_ROTATION || v->kind == SL_VEL_SWIRL)) return false;
   if (c->mesh.dim == 2 && v->kind == SL_VEL_SINX) return false;
   if (v->kind == SL_VEL_SWIRL && !(v->p[0] != 0.0)) return false;
@@ -519,6 +523,8 @@ sl_status check_step(sl_ctx* c, const void* phi_in, const void* phi_out, const s
   if (((uintptr_t)phi_in | (uintptr_t)phi_out) & 15u)
     return fail(c, SL_EINVAL, "state buffers must be 16-byte aligned");
   if (!valid_velocity(c, vel)) return fail(c, SL_EINVAL, "bad velocity for this mesh");
+  if (vel->kind == SL_VEL_NODAL && (c->precision != SL_FP64 || c->mapped || !c->geo_host.empty()))
+    return fail(c, SL_EUNSUPPORTED, "a nodal velocity is read by the FP64 paths of one-node-count meshes");
   if (opt->rk_order < 1 || opt->rk_order > 4) return fail(c, SL_EINVAL, "rk_order must be 1..4");
   if (opt->fit != SL_FIT_HARD && opt->fit != SL_FIT_SOFT) return fail(c, SL_EINVAL, "bad fit mode");
   if (opt->bvalue != SL_BV_INTERP && opt->bvalue != SL_BV_BACKTRACK) return fail(c, SL_EINVAL, "bad bvalue");
@@ -713,6 +719,8 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
   P.picard_rtol = opt->picard_rtol > 0.0 ? opt->picard_rtol : 1e-13;
   P.picard_cap = opt->picard_cap > 0 ? opt->picard_cap : 60;
   P.gtab = c->inflow_step;
+  P.nodal = vel->kind == SL_VEL_NODAL ? vel->nodal : nullptr;
+  P.nvals = c->nvals;
 
   const double* T = c->d_tables;
   const size_t* off = c->table_off[lin][opt->fit == SL_FIT_SOFT];
@@ -855,7 +863,8 @@ sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, do
   std::vector<double> key = {(double)vel->kind, t0, dt, (double)nsteps, (double)opt->constraints,
                              (double)opt->rk_order, (double)opt->fit, (double)opt->bvalue, opt->picard_rtol,
                              (double)opt->picard_cap, (double)(uintptr_t)phi_a, (double)(uintptr_t)phi_b,
-                             (double)(uintptr_t)c->inflow, (double)c->inflow_stride};
+                             (double)(uintptr_t)c->inflow, (double)c->inflow_stride,
+                             (double)(uintptr_t)vel->nodal, (double)vel->nodal_step};
   for (int i = 0; i < 6; ++i) key.push_back(vel->p[i]);
   if (!c->run_valid || key != c->run_key) {
     if (c->run_exec) cudaGraphExecDestroy(c->run_exec);
@@ -896,7 +905,9 @@ sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, do
     for (int s = 0; s < nsteps && st == SL_OK; ++s) {
       if (batch) c->geo_override = c->d_geo_run + (size_t)s * c->nprob;
       c->inflow_step = c->inflow ? c->inflow + (int64_t)s * c->inflow_stride : nullptr;
-      st = step_dispatch(c, a, b, vel, t0 + s * dt, dt, opt);
+      sl_velocity vs = *vel;                 // a nodal field advances by nodal_step per step
+      if (vs.kind == SL_VEL_NODAL) vs.nodal += (int64_t)s * vs.nodal_step;
+      st = step_dispatch(c, a, b, &vs, t0 + s * dt, dt, opt);
       std::swap(a, b);
     }
     cudaGraph_t graph = nullptr;
@@ -956,7 +967,9 @@ sl_status sl_run_host(sl_ctx* c, const double* host_in, double* host_out, const 
   const double* inflow0 = c->inflow;        // step s reads record s
   for (int s = 0; s < nsteps; ++s) {
     c->inflow = inflow0 ? inflow0 + (int64_t)s * c->inflow_stride : nullptr;
-    sl_status st = sl_step(c, a, b, vel, t0 + s * dt, dt, opt);
+    sl_velocity vs = *vel;                   // a nodal field advances by nodal_step per step
+    if (vs.kind == SL_VEL_NODAL) vs.nodal += (int64_t)s * vs.nodal_step;
+    sl_status st = sl_step(c, a, b, &vs, t0 + s * dt, dt, opt);
     c->inflow = inflow0;
     if (st != SL_OK) return st;
     std::swap(a, b);

@@ -16,6 +16,8 @@ namespace sl {
 constexpr int NMAX = 17;                 // largest node count per direction
 constexpr int MMAX1D = 3;                // linear constraint rows in 1D: left, right, mass
 constexpr double TIE = 1e-13;            // |u.n| at or below this is an upwind tie
+// SL_VEL_NODAL: a point within this of a face, relative to |x0| + |x1| (|y0| + |y1|), is on it
+constexpr double FACE_RTOL = 1e-12;
 // The energy row is applied only when the linear fit misses the energy target by more than this,
 // relative (Sec. 4.3: the iteration starts from the linear fit and stops when iterates agree).
 // FP64 paths decide one decade above the double rounding level of the energy sums.  The mixed
@@ -83,6 +85,8 @@ struct StepParams {
   double picard_rtol;
   int picard_cap;
   const double* gtab;                    // 1D inflow record of this step (sl_set_inflow), or null
+  const double* nodal;                   // SL_VEL_NODAL: [2][dim][nvals] node velocities at t, t + dt
+  int64_t nvals;                         // state values (stride of the nodal components)
 };
 
 void launch_step1d_f64(int n, const StepParams& p, const Tables1D& tb, const double* in,

@@ -1,0 +1,141 @@
+"""GPU parity of nodal velocity input (SL_VEL_NODAL: the velocity given at the solution nodes,
+Sec. 4.2) on the FP64 paths against the oracle's nodal field (reading R15).  Fields with non-zero
+divergence exercise the value equation (eq. 4.8); a time series of node velocities advances
+through sl_run by nodal_step.  Bound: relative L2 <= 1e-12 per step."""
+import numpy as np
+import pytest
+
+from oracle import sl_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def sl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_06476_gb300 import build as B
+    B.build()
+    import paper_1910_06476_gb300 as pkg
+    return pkg
+
+
+def ufield_1d(x, t):
+    return 0.8 - 0.5 * np.sin(2 * np.pi * x) * (1.0 + 0.3 * t)
+
+
+def uv_field_2d(x, y, t):
+    u = 0.6 + 0.2 * np.sin(2 * np.pi * y) + 0.1 * np.sin(2 * np.pi * x) * (1 + t)
+    v = -0.3 + 0.15 * np.cos(2 * np.pi * x) + 0.1 * np.cos(2 * np.pi * y)
+    return u, v
+
+
+def series_1d(x, times):
+    return np.stack([ufield_1d(x, t) for t in times])               # [T][...]
+
+
+def series_2d(x, y, times):
+    return np.stack([np.stack(uv_field_2d(x, y, t)) for t in times])  # [T][2][...]
+
+
+@pytest.mark.parametrize("bc,cons,rk,fit,bvalue", [(0, 1, 4, 0, 0), (0, 3, 4, 0, 0), (0, 7, 4, 0, 0), (0, 3, 2, 1, 0),
+                                                   (0, 3, 3, 0, 1), (1, 3, 4, 0, 0), (1, 1, 1, 1, 1)])
+def test_nodal_1d_parity(sl, bc, cons, rk, fit, bvalue):
+    K, n, box = 7, 8, (0.0, 1.0, 0.0, 0.0)
+    ctx = sl.Context(1, K, 1, box, n, sl.GAUSS_LEGENDRE, sl.FP64, (bc,) * 4, 0.25)
+    setup = O.Setup(1, K, 1, box, n, O.GAUSS_LEGENDRE, (bc,) * 4, 0.25)
+    x, _ = ctx.node_coords()
+    x = x.reshape(K, n)
+    t0 = 0.2
+    umax = 1.8
+    dt = 0.9 * ctx.max_dt(sl.velocity(sl.VEL_CONST, umax), sl.RULE_PAPER)
+    times = [t0 + k * dt for k in range(4)]
+    U = series_1d(x, times)                                          # [4][K][n]
+    dev = torch.tensor(U.ravel(), device="cuda")
+    phi0 = 1.0 + 0.3 * np.cos(2 * np.pi * x) + 0.05 * np.sin(6 * np.pi * x)
+    opts = sl.options(cons, rk, fit, bvalue)
+    vel = sl.nodal_velocity(dev, umax)
+    a = torch.tensor(phi0.ravel(), device="cuda")
+    b = torch.empty_like(a)
+    ctx.step(a, b, vel, t0, dt, opts)
+    assert ctx.sync() == 0
+    f = O.NodalField(setup, times[0], times[1], U[0], U[1])
+    ref, _ = O.step_1d(setup, phi0, O.StepOpts(O.Vel(O.VEL_NODAL, (), f), t0, dt, cons, rk, fit, bvalue))
+    assert O.rel_l2(setup, b.cpu().numpy().reshape(K, n), ref) <= TOL
+    # three steps of the time series: step k reads arrays k and k + 1
+    vel = sl.nodal_velocity(dev, umax, step=K * n)
+    out = ctx.run(torch.tensor(phi0.ravel(), device="cuda"), torch.empty_like(a), vel, t0, dt, 3, opts)
+    assert ctx.sync() == 0
+    ph = phi0
+    for k in range(3):
+        f = O.NodalField(setup, times[k], times[k + 1], U[k], U[k + 1])
+        ph, _ = O.step_1d(setup, ph, O.StepOpts(O.Vel(O.VEL_NODAL, (), f), times[k], dt, cons, rk, fit, bvalue))
+    assert O.rel_l2(setup, out.cpu().numpy().reshape(K, n), ph) <= TOL
+
+
+@pytest.mark.parametrize("kx,ky,n,bc,cons,rk,bvalue", [(4, 3, 5, 0, 3, 4, 0), (3, 3, 6, 0, 3, 4, 0),
+                                                       (3, 4, 5, 1, 3, 4, 0), (3, 3, 5, 0, 3, 3, 1),
+                                                       (2, 2, 8, 1, 1, 2, 0)])
+def test_nodal_2d_parity(sl, kx, ky, n, bc, cons, rk, bvalue):
+    box = (0.0, 1.0, 0.0, 1.0)
+    ctx = sl.Context(2, kx, ky, box, n, sl.GAUSS_LEGENDRE, sl.FP64, (bc,) * 4, 0.15)
+    setup = O.Setup(2, kx, ky, box, n, O.GAUSS_LEGENDRE, (bc,) * 4, 0.15)
+    x, y = ctx.node_coords()
+    t0 = 0.1
+    umax, vmax = 1.05, 0.6
+    dt = 0.9 * ctx.max_dt(sl.velocity(sl.VEL_CONST, umax, vmax), sl.RULE_PAPER)
+    times = [t0 + k * dt for k in range(3)]
+    U = series_2d(x, y, times)                                       # [3][2][ky][kx][n][n]
+    dev = torch.tensor(U.ravel(), device="cuda")
+    phi0 = 1.0 + 0.4 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    opts = sl.options(cons, rk, 0, bvalue)
+    vel = sl.nodal_velocity(dev, umax, vmax, step=2 * x.size)
+    out = ctx.run(torch.tensor(phi0.ravel(), device="cuda"), torch.empty(x.size, device="cuda", dtype=torch.float64),
+                  vel, t0, dt, 2, opts)
+    bits = ctx.sync()
+    ph = phi0
+    conv = True
+    for k in range(2):
+        f = O.NodalField(setup, times[k], times[k + 1], U[k][0], U[k + 1][0], U[k][1], U[k + 1][1])
+        ph, infos = O.step_2d(setup, ph, O.StepOpts(O.Vel(O.VEL_NODAL, (), f), times[k], dt, cons, rk, 0, bvalue))
+        conv = conv and all(i["converged"] for i in infos.values())
+    assert conv and bits == 0, bits
+    assert O.rel_l2(setup, out.cpu().numpy().reshape(ky, kx, n, n), ph) <= TOL
+
+
+def test_nodal_rotation_matches_rotation_kind(sl):
+    """Node samples of the solid-body rotation step like SL_VEL_ROTATION on the GPU (a linear field
+    is its own interpolant)."""
+    ctx = sl.Context(2, 4, 4, (0.0, 1.0, 0.0, 1.0), 6, 0, sl.FP64, (1,) * 4, 0.0)
+    x, y = ctx.node_coords()
+    om = 2 * np.pi
+    u, v = -om * (y - 0.5), om * (x - 0.5)
+    dev = torch.tensor(np.stack([u, v, u, v]).ravel(), device="cuda")
+    rot = sl.velocity(sl.VEL_ROTATION, om, 0.5, 0.5)
+    dt = ctx.max_dt(rot, sl.RULE_PAPER)
+    phi = torch.tensor(np.exp(-((x - 0.35) ** 2 + (y - 0.5) ** 2) / 0.02).ravel(), device="cuda")
+    a, b = torch.empty_like(phi), torch.empty_like(phi)
+    opts = sl.options(3, 4)
+    ctx.step(phi, a, rot, 0.0, dt, opts)
+    ctx.step(phi, b, sl.nodal_velocity(dev, om * 0.5, om * 0.5), 0.0, dt, opts)
+    assert ctx.sync() == 0
+    assert (a - b).abs().max().item() <= 1e-12 * phi.abs().max().item()
+
+
+def test_nodal_rejected_where_unsupported(sl):
+    cm = sl.Context(2, 2, 2, (0.0, 1.0, 0.0, 1.0), 4, 0, sl.MIXED, (0,) * 4, 0.0)
+    dev = torch.zeros(4 * 64, device="cuda", dtype=torch.float64)
+    a = cm.new_state()
+    with pytest.raises(sl.SlError):
+        cm.step(a, cm.new_state(), sl.nodal_velocity(dev, 1.0, 1.0), 0.0, 1e-3, sl.options(1, 4))
+    c = sl.Context(1, 4, 1, (0.0, 1.0, 0.0, 0.0), 5, 0, sl.FP64, (0,) * 4, 0.0)
+    bad = sl.velocity(sl.VEL_NODAL, 1.0)                             # null array
+    z = torch.zeros(20, device="cuda", dtype=torch.float64)
+    with pytest.raises(sl.SlError):
+        c.step(z, torch.empty_like(z), bad, 0.0, 1e-3, sl.options(1, 4))
+    with pytest.raises(sl.SlError):                                 # the caller's bound enters the CFL check
+        c.step(z, torch.empty_like(z), sl.nodal_velocity(dev, 10.0), 0.0, 0.1, sl.options(1, 4))
