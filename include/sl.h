@@ -112,8 +112,13 @@ enum { SL_FIT_HARD = 0, SL_FIT_SOFT = 1 };
  * (eq. remap_bnd); SL_BV_BACKTRACK evaluates phi^n at the backward foot (eq. 4.11). */
 enum { SL_BV_INTERP = 0, SL_BV_BACKTRACK = 1 };
 
-/* Time-step rules for sl_max_dt (eq. 1d_delt_condition, 2d_delt_condition). */
-enum { SL_RULE_HALF_MIN_SPACING = 0, SL_RULE_PAPER = 1 };
+/* Time-step rules for sl_max_dt (eq. 1d_delt_condition, 2d_delt_condition): half the minimum
+ * spacing between adjacent nodes; the paper's step (the gap from the element edge to its first
+ * node, factor 1: no particle leaves its element); half the paper's step.  Measured on the 2D
+ * deforming flows (swirl, solid-body rotation with inflow walls) at fine meshes and n >= 8, the
+ * paper's step sits at the stability limit: perturbations grow without bound (both precisions,
+ * every constraint set, fit and interface rule), where half of it stays bounded. */
+enum { SL_RULE_HALF_MIN_SPACING = 0, SL_RULE_PAPER = 1, SL_RULE_HALF_PAPER = 2 };
 
 /* Sticky device status bits (sl_sync). */
 enum {

@@ -52,7 +52,8 @@ in the design notes):
       non-periodic domain faces keep their own trace.
   R9  Time step (eq. 1d_delt_condition, 2d_delt_condition): rule 'paper' uses the gap from
       the element edge to the first node with factor 1; rule 'half_min_spacing' uses half
-      the minimum spacing between adjacent nodes.
+      the minimum spacing between adjacent nodes; rule 'half_paper' half the paper's step
+      (R16: the step the 2D deforming flows are run at).
   R10 p-nonconforming faces: the upwind neighbour's polynomial is evaluated at this element's
       face points; face fluxes use the Gauss rule of the side with more nodes.
   R15 Nodal velocity (Sec. 4.2, a velocity given at the Gauss nodes by an Eulerian solver):
@@ -413,7 +414,7 @@ def max_dt(setup, vel, rule="half_min_spacing", cfl=None):
         gap = min(gaps)
     else:
         gap = np.min(np.diff(xi)) if rule == "half_min_spacing" else xi[0]
-    factor = (0.5 if rule == "half_min_spacing" else 1.0) if cfl is None else cfl
+    factor = (1.0 if rule == "paper" else 0.5) if cfl is None else cfl
     umax, vmax = max_speed(vel, setup.box)
     lims = []
     if umax > 0:

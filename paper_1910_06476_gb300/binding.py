@@ -22,7 +22,7 @@ VEL_CONST, VEL_ROTATION, VEL_SWIRL, VEL_SINX, VEL_NODAL = 0, 1, 2, 3, 4
 C_BOUNDARY, C_MASS, C_ENERGY = 1, 2, 4
 FIT_HARD, FIT_SOFT = 0, 1
 BV_INTERP, BV_BACKTRACK = 0, 1
-RULE_HALF_MIN_SPACING, RULE_PAPER = 0, 1
+RULE_HALF_MIN_SPACING, RULE_PAPER, RULE_HALF_PAPER = 0, 1, 2
 ST_NONFINITE, ST_PICARD_NOCONV, ST_SOLVE_NOCONV, ST_TIMEOUT, ST_SOLVE_FLOOR = 1, 2, 4, 8, 16
 COUNTERS = ("elems", "solve_iters", "solve_floor", "solve_noconv", "energy_applied", "picard_iters",
             "picard_noconv", "feet")

@@ -1094,17 +1094,19 @@ sl_status sl_counters(sl_ctx* c, uint64_t* counts) {
 sl_status sl_max_dt(const sl_ctx* c, const sl_velocity* vel, int rule, double* dt) {
   if (!c || !dt) return SL_EINVAL;
   if (!valid_velocity(c, vel)) return fail(const_cast<sl_ctx*>(c), SL_EINVAL, "bad velocity");
-  if (rule != SL_RULE_HALF_MIN_SPACING && rule != SL_RULE_PAPER) return fail(const_cast<sl_ctx*>(c), SL_EINVAL, "bad rule");
+  if (rule != SL_RULE_HALF_MIN_SPACING && rule != SL_RULE_PAPER && rule != SL_RULE_HALF_PAPER)
+    return fail(const_cast<sl_ctx*>(c), SL_EINVAL, "bad rule");
+  const bool edge = rule != SL_RULE_HALF_MIN_SPACING;
   // smallest gap over the node counts in use: edge node to face (paper) or between nodes
   double gap = 1.0;
   for (int n = 2; n <= NMAX; ++n) {
     if (!c->nt[n].present) continue;
     const std::vector<double>& xi = c->nt[n].b.xi;
-    if (rule == SL_RULE_PAPER) gap = std::min(gap, xi[0]);
+    if (edge) gap = std::min(gap, xi[0]);
     else
       for (size_t i = 1; i < xi.size(); ++i) gap = std::min(gap, xi[i] - xi[i - 1]);
   }
-  const double factor = rule == SL_RULE_PAPER ? 1.0 : 0.5;
+  const double factor = rule == SL_RULE_PAPER ? 1.0 : 0.5;     // half-spacing and half-paper: 0.5
   double lim = INFINITY;
   const std::vector<sl_mesh> one(1, c->mesh);
   for (const sl_mesh& M : c->prob_mesh.empty() ? one : c->prob_mesh) {

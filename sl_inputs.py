@@ -55,7 +55,8 @@ class Problem:
     t0: float = 0.0
     phi0: object = None     # callable phi0(x[, y]) -> array (plain numpy)
     orders: object = None   # optional per-element node counts (p-adaptive), shape (ky, kx)
-    dt_rule: str = "paper"  # "paper": edge-node gap, factor 1; "half_min_spacing": half the min spacing
+    dt_rule: str = "paper"  # "paper": edge-node gap, factor 1; "half_min_spacing": half the min spacing;
+                            # "half_paper": half the paper's step (the 2D deforming flows)
     extra: dict = field(default_factory=dict)
 
 
@@ -131,14 +132,14 @@ def config4_rotation(k=256, seed=0, uniform_n=None):
         orders = p_adaptive_orders(k, k, seed)
     return Problem(f"2d_rotation_K{k}x{k}", 2, k, k, (0.0, 1.0, 0.0, 1.0), n, GAUSS_LEGENDRE,
                    Velocity(VEL_ROTATION, (2.0 * np.pi, 0.5, 0.5, 0, 0, 0)), (BC_INFLOW,) * 4, 0.0,
-                   C_BOUNDARY | C_MASS, 4, phi0=hill_2d, orders=orders)
+                   C_BOUNDARY | C_MASS, 4, phi0=hill_2d, orders=orders, dt_rule="half_paper")
 
 
 def config5_swirl(n=8, k=2048, T=5.0):
     """2D swirling deformation flow with period T = 5, cosine bell, mass + energy (+ boundary)."""
     return Problem(f"2d_swirl_K{k}x{k}_n{n}", 2, k, k, (0.0, 1.0, 0.0, 1.0), n, GAUSS_LEGENDRE,
                    Velocity(VEL_SWIRL, (T, 0, 0, 0, 0, 0)), (BC_INFLOW,) * 4, 0.0,
-                   C_BOUNDARY | C_MASS | C_ENERGY, 4, phi0=cosine_bell_2d)
+                   C_BOUNDARY | C_MASS | C_ENERGY, 4, phi0=cosine_bell_2d, dt_rule="half_paper")
 
 
 def p_adaptive_orders(kx, ky, seed):
@@ -191,8 +192,9 @@ def sample_elements(count, total, seed):
 
 
 def rule_code(prob):
-    """Time-step rule of a problem as the C ABI enumeration (0: half min spacing, 1: paper)."""
-    return 1 if prob.dt_rule == "paper" else 0
+    """Time-step rule of a problem as the C ABI enumeration (0: half min spacing, 1: paper,
+    2: half the paper's step)."""
+    return {"half_min_spacing": 0, "paper": 1, "half_paper": 2}[prob.dt_rule]
 
 
 def steps_to(T, dt0):

@@ -178,16 +178,14 @@ def test_mixed2d_config3_500_steps(sl):
 
 
 def test_mixed2d_swirl_against_fp64(sl):
-    """Config 5's problem (swirl, cosine bell, boundary + mass + energy), n = 8, 512 x 512, with the
-    paper's time step.  On this flow the discrete scheme itself amplifies small perturbations
-    transiently inside the bell (near x = 0.48, y = 0.72): in FP64 a 1e-12 perturbation grows to
-    7e-3 within 1000 steps (test_gpu_stability), so no two implementations that differ at
-    rounding level stay within 1e-6 for 1000 steps there.  The mixed path is compared over 200
-    steps, before that amplification, against the 1e-6 bound."""
-    prob = sl_inputs.config5_swirl(n=8, k=512)
-    c64, cm, a64, am, errs, m0 = _long_run(sl, prob, 8, 200, sl.VEL_SWIRL, (5.0,))
+    """Config 5's problem (swirl, cosine bell, boundary + mass + energy), n = 8, 256 x 256, at its
+    configured step (half the paper's), 1000 steps: mixed against the FP64 GPU path within the
+    1e-6 bound.  On this flow the scheme amplifies rounding-level differences transiently inside
+    the bell (test_gpu_stability), which is what the bound has to absorb."""
+    prob = sl_inputs.config5_swirl(n=8, k=256)
+    c64, cm, a64, am, errs, m0 = _long_run(sl, prob, 8, 1000, sl.VEL_SWIRL, (5.0,))
     b64, bm = c64.sync(), cm.sync()
-    assert errs[1] <= TOL and errs[200] <= TOL, (errs, b64, bm)
+    assert errs[1] <= TOL and errs[1000] <= TOL, (errs, b64, bm)
     assert b64 & ~sl.ST_PICARD_NOCONV == 0 and bm & ~sl.ST_PICARD_NOCONV == 0, (b64, bm)
 
 
