@@ -67,24 +67,27 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_final(int nparts, const double*
   if (threadIdx.x == 0) *out = red[0] * scale;
 }
 
-// Device address of g_partials, looked up once per device with that device current.  In host
-// code the symbol g_partials is only a host-side stand-in and must never be passed to a kernel.
+// Device address of g_partials, looked up with that device current and kept once the lookup has
+// succeeded (a failed lookup is retried by the next call).  In host code the symbol g_partials is
+// only a host-side stand-in and must never be passed to a kernel.  The address belongs to the
+// device's primary context: a cudaDeviceReset ends that context, and the entry point must not be
+// used on that device afterwards.
 constexpr int NA_MAX_DEVICES = 64;
-std::once_flag g_once[NA_MAX_DEVICES];
+std::mutex g_mu;
 double* g_addr[NA_MAX_DEVICES] = {};
-cudaError_t g_err[NA_MAX_DEVICES] = {};
 
 cudaError_t scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::call_once(g_once[dev], [dev] {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
     void* p = nullptr;
-    g_err[dev] = cudaGetSymbolAddress(&p, g_partials);
+    e = cudaGetSymbolAddress(&p, g_partials);
+    if (e != cudaSuccess) return e;
     g_addr[dev] = static_cast<double*>(p);
-  });
-  if (g_err[dev] != cudaSuccess) return g_err[dev];
+  }
   *out = g_addr[dev];
   return cudaSuccess;
 }

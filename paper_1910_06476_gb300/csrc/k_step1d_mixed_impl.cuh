@@ -333,11 +333,21 @@ __global__ void __launch_bounds__(TILE, NN <= 11 ? 3 : 2)
     }
     bool arrived = false;
     for (int it = 0; it < WAIT_LIMIT && !arrived; ++it) arrived = mbar_try_wait(&bar[st], (parity >> st) & 1u);
-    parity ^= 1u << st;
     if (__syncthreads_or(!arrived)) {             // every thread leaves together
       bits |= SL_ST_TIMEOUT;
+      // the loads still in flight into this stage and into the prefetched one must land before
+      // the CTA's shared memory is released: one more bounded wait on each (the output is left
+      // incomplete either way)
+      if (tid == 0) {
+        bool done = false;
+        for (int it = 0; it < WAIT_LIMIT && !done; ++it) done = mbar_try_wait(&bar[st], (parity >> st) & 1u);
+        done = tn >= ntiles;
+        for (int it = 0; it < WAIT_LIMIT && !done; ++it) done = mbar_try_wait(&bar[st ^ 1], (parity >> (st ^ 1)) & 1u);
+      }
+      __syncthreads();
       break;
     }
+    parity ^= 1u << st;
     const TileGeo g = tile_geo<NN>(P, t);
     float* shi = sm + st * 2 * SF;
     float* slo = shi + SF;

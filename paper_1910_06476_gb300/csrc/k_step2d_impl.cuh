@@ -18,6 +18,8 @@
 // phihat <- phihat + M^{-1} (phi* - H phihat), with M = A_y (x) A_x the exact matrix of a uniform
 // shift by the element's mean particle displacement, whose inverse is the 1D remap R_y (x) R_x.
 // H phihat costs n^2 per particle (the advected basis values are kept in registers).
+#include <cfloat>
+
 #include "k_map2d.cuh"
 
 namespace sl {
@@ -371,7 +373,9 @@ __global__ void __launch_bounds__(Shape<NN>::NT) k_p1(StepParams P0, Tables1D tb
       s_r[tid] = r;
     }
     const double rmax = block_max<NT>(fabs(r), s_red);
-    if (rmax <= SOLVE_RTOL * scale || rmax == 0.0) { solved = true; break; }
+    // (data near the bottom of the double range carry no relative accuracy: a residual below
+    // DBL_MIN / DBL_EPSILON, about 1e-292, is at the floor of the arithmetic)
+    if (rmax <= SOLVE_RTOL * scale || rmax <= DBL_MIN / DBL_EPSILON) { solved = true; break; }
     // a residual that has stopped improving at the rounding floor counts as converged
     if (rmax > 0.5 * prev && rmax <= SOLVE_STALL * scale) { solved = true; break; }
     prev = rmax;

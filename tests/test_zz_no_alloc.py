@@ -65,3 +65,30 @@ def test_noalloc_rejects_inputs_beyond_its_scratch(sl):
                                  C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == sl.SL_EINVAL
     assert b"SL_NOALLOC_MAX_VALUES" in lib.sl_last_error(None)
+
+
+def test_noalloc_inside_global_mode_capture(sl):
+    """The use the entry point exists for: after one eager call on the device, a call recorded
+    under global-mode stream capture (where allocation is forbidden) and replayed from the graph
+    gives the integral of whatever the input buffer holds at replay time."""
+    lib = sl.lib()
+    K, n = 500, 9
+    ctx = sl.Context(1, K, 1, (0.0, 1.0, 0.0, 0.0), n, sl.GAUSS_LEGENDRE, sl.FP64, (0, 0, 0, 0), 0.0)
+    _, w = ctx.nodes_weights()
+    w_host = np.ascontiguousarray(w, dtype=np.float64)
+    phi = torch.tensor(1.5 + sl_inputs.random_state((ctx.size,), 3), device="cuda")
+    _noalloc(lib, phi, K, n, 1, w, 1, 1.0 / K, torch.cuda.current_stream())      # first call, eager
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        st = lib.sl_integral_noalloc(C.c_void_p(phi.data_ptr()), K, n, 1, w_host.ctypes.data_as(C.c_void_p), 1,
+                                     1.0 / K, C.c_void_p(out.data_ptr()),
+                                     C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, lib.sl_last_error(None)
+    for seed in (4, 5):
+        phi.copy_(torch.tensor(0.5 + sl_inputs.random_state((ctx.size,), seed), device="cuda"))
+        g.replay()
+        torch.cuda.synchronize()
+        ref = ctx.mass(phi)
+        assert abs(out.item() - ref) <= 1e-13 * abs(ref), (seed, out.item(), ref)
