@@ -453,7 +453,8 @@ def run_ours(args, rank, world, local_rank):
     dom_ms = max(p1_avg, p2_avg)
     dom_f = f1 if p1_avg >= p2_avg else f2
     roof = {"bound": "alu", "achieved": dom_f / (dom_ms * 1e-3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": dom_f / (dom_ms * 1e-3) / 1e12 / fp32_peak, "traffic": TRAFFIC.get(dom["kernel"].split(" ")[0]),
+            "frac": dom_f / (dom_ms * 1e-3) / 1e12 / fp32_peak, "traffic": (TRAFFIC_PER_ELEMENT[dom["kernel"].split(" ")[0]] * nel
+                        if dom["kernel"].split(" ")[0] in TRAFFIC_PER_ELEMENT else None),
             "kernel": dom["kernel"], "ms_per_launch": dom_ms,
             "peak_source": f"FP32: {FP32_LANES} lanes x 2 x median SM clock {sm_mhz:.0f} MHz under load (unit counts)",
             "flop_model": "bench.flop_model (algorithmic FP32 operations from the measured iteration counts)",
@@ -485,7 +486,12 @@ def run_ours(args, rank, world, local_rank):
 
 # DRAM bytes per launch from one ncu capture (read + written), scaled to the full mesh by the
 # element count (traffic grows in proportion); None once the kernel has changed since
-TRAFFIC = {}
+# DRAM bytes (read + write) per element of the dominant kernels, from one ncu capture at 512 x 512
+# (262,144 elements; traffic grows in proportion to the elements), multiplied by the element count
+# of a launch (profiles/k2m_k_p1_k_p2_mixed_general_config5_swirl.md).  Valid for the kernels as
+# profiled; to be taken again after a change to them.
+TRAFFIC_PER_ELEMENT = {"k2m::k_p1<8>": (139.418112e6 + 89.868288e6) / 262144,
+                       "k2m::k_p2<8>": (272.105728e6 + 113.296384e6) / 262144}
 
 
 def _problem_state(sl, torch, prob, precision):
