@@ -351,6 +351,7 @@ def run_ours(args, rank, world, local_rank):
     phi0_dev = device_initial_state(torch, ctx, prob)
     a = ctx.pack(phi0_dev)
     b = ctx.new_state()
+    tuned = ctx.tune(a, b, vel, 0.0, dt, opts, tune_cache_path())   # launch shapes (sl_tune)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     # one step from t = 0 for the accuracy check against the oracle
     ctx.step(a, b, vel, 0.0, dt, opts)
@@ -467,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32 (double-float state, float-float mass)",
             "data": "synthetic (seeded analytic cosine bell)",
             "config": dict(workload_config(k, n, "mixed"), dt=dt),
-            "roofline": roof, "clocks": clk,
+            "roofline": roof, "clocks": clk, "autotune": tuned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nodes * 8, "d2h_bytes_per_step": nodes * 8,
                     "api": "sl_run_host (pinned host doubles in, one step, host doubles out)"},
             "gpu_launches": 2 * args.steps,
@@ -513,6 +514,7 @@ def measure_config(sl, torch, prob, precision, steps, flush, phi=None):
     opts = sl.options(prob.constraints, prob.rk_order)
     a, b = ctx.pack(phi0), ctx.new_state()
     stream = ctx.stream
+    tuned = ctx.tune(a, b, vel, 0.0, dt, opts, tune_cache_path())   # launch shapes (sl_tune)
     ctx.step(a, b, vel, 0.0, dt, opts)           # warm-up
     torch.cuda.synchronize()
     ms, a, b, _ = _time_steps(torch, ctx, stream, b, a, vel, dt, opts, dt, steps, flush)
@@ -520,8 +522,19 @@ def measure_config(sl, torch, prob, precision, steps, flush, phi=None):
     nodes = ctx.size
     per = ms / steps
     return {"ms_per_step": per, "node_updates_per_s": nodes / (per * 1e-3), "steps": steps,
-            "hbm_frac_of_measured": nodes * 16 / (per * 1e-3) / 1e9 / peaks()[0], "device_status": status}, phi0, (
-        ctx, vel, dt, opts)
+            "hbm_frac_of_measured": nodes * 16 / (per * 1e-3) / 1e9 / peaks()[0], "device_status": status,
+            "autotune": tuned}, phi0, (ctx, vel, dt, opts)
+
+
+def tune_cache_path():
+    """The autotuner's JSON cache: SL_TUNE_CACHE, else the user's cache directory."""
+    p = os.environ.get("SL_TUNE_CACHE")
+    if not p:
+        d = os.path.join(os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache")),
+                         "paper_1910_06476_gb300")
+        os.makedirs(d, exist_ok=True)
+        p = os.path.join(d, "tune.json")
+    return p
 
 
 def secondary_configs(sl, torch, flush, full=False, only=None):

@@ -337,6 +337,23 @@ sl_status sl_counters(sl_ctx* ctx, uint64_t* counts);
 sl_status sl_timing(sl_ctx* ctx, int enable);
 sl_status sl_timing_read(sl_ctx* ctx, double* ms, int* nsteps);
 
+/* Autotuner of the launch shapes of the kernels a step of this context runs with these
+ * arguments.  The 2D shared-operator path (uniform mesh, constant velocity, mixed precision) has
+ * a few compiled tile shapes (elements per CTA) per node count; the 2D general mixed path runs
+ * persistent grids whose resident CTAs per SM can be held below the occupancy limit, per phase.
+ * sl_tune times each candidate with CUDA events on the context's stream (one warm-up and three
+ * timed steps from phi_in to phi_out; phi_in is only read, phi_out is overwritten), keeps the
+ * fastest in the context, and records it under a key naming the device, the path, the mesh, the
+ * node count and the options in the JSON file cache_path (a flat object of string keys and string
+ * values, rewritten through a temporary file; null: no cache).  A key already in the file is
+ * applied without timing.  Other paths have nothing to tune (no timing, default shapes).  Every
+ * shape computes each element with the same arithmetic, so results do not depend on the choice.
+ * choice (host, nullable, 4 ints): the tile index, the CTAs per SM of phase 1 and of phase 2
+ * (0: the occupancy limit), and 1 if the choice came from the cache.  Synchronises the stream.
+ * Errors: those of sl_step; SL_EINVAL for an unreadable or unwritable cache (nothing applied). */
+sl_status sl_tune(sl_ctx* ctx, const void* phi_in, void* phi_out, const sl_velocity* vel, double t, double dt,
+                  const sl_options* opt, const char* cache_path, int* choice);
+
 /* Last error message of the context (or of the last failed sl_init when ctx is null). */
 const char* sl_last_error(const sl_ctx* ctx);
 

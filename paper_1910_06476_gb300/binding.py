@@ -30,7 +30,7 @@ COUNTERS = ("elems", "solve_iters", "solve_floor", "solve_noconv", "energy_appli
 EXPORTS = ["sl_init", "sl_free", "sl_step", "sl_run", "sl_run_host", "sl_pack", "sl_unpack", "sl_mass", "sl_energy",
            "sl_sync", "sl_max_dt", "sl_state_size", "sl_state_bytes", "sl_node_coords", "sl_nodes_weights",
            "sl_integral_noalloc", "sl_batch_create", "sl_batch_step", "sl_batch_offset", "sl_counters",
-           "sl_timing", "sl_timing_read", "sl_set_inflow", "sl_last_error"]
+           "sl_timing", "sl_timing_read", "sl_set_inflow", "sl_tune", "sl_last_error"]
 
 
 class SlMesh(C.Structure):
@@ -78,6 +78,8 @@ def load_library(path=LIB_PATH):
     lib.sl_counters.argtypes = [P, C.POINTER(C.c_uint64)]
     lib.sl_timing.argtypes = [P, C.c_int]
     lib.sl_set_inflow.argtypes = [P, P, C.c_int64]
+    lib.sl_tune.argtypes = [P, P, P, C.POINTER(SlVelocity), C.c_double, C.c_double, C.POINTER(SlOptions), C.c_char_p,
+                            C.POINTER(C.c_int)]
     lib.sl_timing_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.sl_max_dt.argtypes = [P, C.POINTER(SlVelocity), C.c_int, C.POINTER(C.c_double)]
     lib.sl_state_size.argtypes = [P]
@@ -276,6 +278,17 @@ class Context:
             raise ValueError("inflow records: a contiguous CUDA float64 tensor")
         self._check(self._lib.sl_set_inflow(self._h, _ptr(values), int(step_stride)))
         self._inflow = values
+
+    def tune(self, phi_in, phi_out, vel, t, dt, opts, cache_path=None):
+        """Autotune the launch shapes of this step (sl_tune); returns {"tile", "per_sm_phase1",
+        "per_sm_phase2", "cached"}."""
+        self._state(phi_in, "phi_in")
+        self._state(phi_out, "phi_out")
+        out = (C.c_int * 4)()
+        path = None if cache_path is None else str(cache_path).encode()
+        self._check(self._lib.sl_tune(self._h, _ptr(phi_in), _ptr(phi_out), C.byref(vel), float(t), float(dt),
+                                      C.byref(opts), path, out))
+        return {"tile": out[0], "per_sm_phase1": out[1], "per_sm_phase2": out[2], "cached": bool(out[3])}
 
     def timing(self, enable):
         """Start (True) or end (False) a kernel-timing session (sl_timing)."""

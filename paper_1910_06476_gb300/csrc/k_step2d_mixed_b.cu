@@ -4,12 +4,12 @@
 namespace sl {
 namespace k2m {
 template void launch_n<9>(int, const StepParams&, const Mixed2DExtra&, const Map2D&, int64_t, const float*, float*,
-                            const Work2M&, unsigned*, cudaStream_t);
+                            const Work2M&, unsigned*, cudaStream_t, int);
 template void launch_n<10>(int, const StepParams&, const Mixed2DExtra&, const Map2D&, int64_t, const float*, float*,
-                            const Work2M&, unsigned*, cudaStream_t);
+                            const Work2M&, unsigned*, cudaStream_t, int);
 template void launch_n<11>(int, const StepParams&, const Mixed2DExtra&, const Map2D&, int64_t, const float*, float*,
-                            const Work2M&, unsigned*, cudaStream_t);
+                            const Work2M&, unsigned*, cudaStream_t, int);
 template void launch_n<12>(int, const StepParams&, const Mixed2DExtra&, const Map2D&, int64_t, const float*, float*,
-                            const Work2M&, unsigned*, cudaStream_t);
+                            const Work2M&, unsigned*, cudaStream_t, int);
 }  // namespace k2m
 }  // namespace sl

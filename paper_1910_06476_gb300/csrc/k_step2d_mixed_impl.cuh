@@ -1450,14 +1450,16 @@ __global__ void __launch_bounds__(Shape<NN>::NT, Shape<NN>::MINB2)
 // persistent grid: the resident CTAs of the whole GPU, or one CTA per EPC elements if fewer
 template <int NN>
 void launch_n(int phase, const StepParams& p, const Mixed2DExtra& x, const Map2D& m, int64_t count, const float* in,
-              float* out, const Work2M& w, unsigned* st, cudaStream_t s) {
+              float* out, const Work2M& w, unsigned* st, cudaStream_t s, int per_sm) {
   if (count <= 0) return;
   using S = Shape<NN>;
   // phase 2 stages the fit operator for the largest row set (4 n + 1 rows), whatever p.m is, so
   // that one occupancy figure serves every launch
   const size_t smem2 = (size_t)(4 * NN + 1) * S::ND * sizeof(float);
-  const int fill = phase == 1 ? persistent_grid((const void*)k_p1<NN>, S::NT, 0)
-                              : persistent_grid((const void*)k_p2<NN>, S::NT, smem2);
+  const void* kern = phase == 1 ? (const void*)k_p1<NN> : (const void*)k_p2<NN>;
+  int fill = persistent_grid(kern, S::NT, phase == 1 ? 0 : smem2);
+  // per_sm > 0: that many resident CTAs per SM (the autotuner's choice), within the occupancy
+  if (per_sm > 0) fill = std::min(fill, per_sm * sm_count());
   const int64_t want = (count + S::EPC - 1) / S::EPC;
   const unsigned grid = (unsigned)(want < fill ? want : fill);
   if (phase == 1) k_p1<NN><<<grid, S::NT, 0, s>>>(p, x, m, count, in, w, st);

@@ -2,6 +2,7 @@
 // dispatch of the step kernels, deterministic diagnostics and the host-buffer run.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -184,6 +185,23 @@ void build_rules(int basis, TableBufs& B, size_t& off, size_t& foff) {
 
 namespace sl {
 void set_global_error(const std::string& msg) { g_init_err = msg; }
+
+int sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  cache.emplace(dev, sms);
+  return sms;
+}
 
 int persistent_grid(const void* kernel, int threads, size_t smem) {
   static std::mutex mu;
@@ -648,7 +666,8 @@ sl_status step2d_general(sl_ctx* c, StepParams P, const sl_velocity* vel, double
         }
         float* W = (float*)c->d_work;
         Work2M w{W, W + c->nvals, W + c->nvals + nel * ts, W + c->nvals + nel * (ts + WORK2M_FACE)};
-        launch_step2d_mixed(phase, n, P, X, map, count, (const float*)in, (float*)out, w, c->d_status, c->stream);
+        launch_step2d_mixed(phase, n, P, X, map, count, (const float*)in, (float*)out, w, c->d_status, c->stream,
+                            c->k2m_per_sm[phase - 1]);
         SL_CUDA(c, cudaGetLastError());
       }
     }
@@ -761,7 +780,8 @@ sl_status step_dispatch(sl_ctx* c, const void* phi_in, void* phi_out, const sl_v
     sl_status st = ensure_m2c(c, vel, dt, opt);
     if (st != SL_OK) return st;
     c->m2c.plane = plane_stride(c->nvals);
-    launch_step2d_const(c->m2c, c->d_m2c, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream);
+    launch_step2d_const(c->m2c, c->d_m2c, (const float*)phi_in, (float*)phi_out, c->d_status, c->stream,
+                        c->k2c_tile);
   } else if (M.dim == 2 && c->precision == SL_MIXED) {
     if (opt->bvalue != SL_BV_INTERP && c->mapped)
       return fail(c, SL_EUNSUPPORTED, "backtracked interface values need a mesh of one node count");
@@ -1164,3 +1184,184 @@ sl_status sl_nodes_weights(const sl_ctx* c, int n, double* xi, double* w) {
 const char* sl_last_error(const sl_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------ autotuner
+
+namespace {
+
+// The cache file: one flat JSON object of string keys and string values (no escapes needed: keys
+// and values are built here from names, numbers and separators).
+bool read_tune_cache(const std::string& path, std::map<std::string, std::string>& out) {
+  out.clear();
+  FILE* f = std::fopen(path.c_str(), "rb");
+  if (!f) return true;                       // no file yet: an empty cache
+  std::string text;
+  char buf[4096];
+  size_t k;
+  while ((k = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, k);
+  std::fclose(f);
+  size_t i = 0;
+  auto skip = [&] {
+    while (i < text.size() && (text[i] == ' ' || text[i] == '\n' || text[i] == '\r' || text[i] == '\t')) ++i;
+  };
+  auto str = [&](std::string& s) {
+    skip();
+    if (i >= text.size() || text[i] != '"') return false;
+    const size_t e = text.find('"', i + 1);
+    if (e == std::string::npos) return false;
+    s = text.substr(i + 1, e - i - 1);
+    i = e + 1;
+    return true;
+  };
+  skip();
+  if (i >= text.size()) return true;
+  if (text[i] != '{') return false;
+  ++i;
+  skip();
+  if (i < text.size() && text[i] == '}') return true;
+  for (;;) {
+    std::string key, val;
+    if (!str(key)) return false;
+    skip();
+    if (i >= text.size() || text[i] != ':') return false;
+    ++i;
+    if (!str(val)) return false;
+    out[key] = val;
+    skip();
+    if (i < text.size() && text[i] == ',') { ++i; continue; }
+    if (i < text.size() && text[i] == '}') return true;
+    return false;
+  }
+}
+
+bool write_tune_cache(const std::string& path, const std::map<std::string, std::string>& m) {
+  const std::string tmp = path + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return false;
+  std::fputs("{\n", f);
+  size_t k = 0;
+  for (const auto& kv : m)
+    std::fprintf(f, "  \"%s\": \"%s\"%s\n", kv.first.c_str(), kv.second.c_str(), ++k < m.size() ? "," : "");
+  std::fputs("}\n", f);
+  const bool ok = std::fclose(f) == 0;
+  return ok && std::rename(tmp.c_str(), path.c_str()) == 0;
+}
+
+std::mutex g_tune_mu;                        // one cache read-modify-write at a time in this process
+
+}  // namespace
+
+sl_status sl_tune(sl_ctx* c, const void* phi_in, void* phi_out, const sl_velocity* vel, double t, double dt,
+                  const sl_options* opt, const char* cache_path, int* choice) {
+  if (!c) return SL_EINVAL;
+  sl_status st = check_step(c, phi_in, phi_out, vel, opt);
+  if (st != SL_OK) return st;
+  if (!c->geo_host.empty()) return fail(c, SL_EUNSUPPORTED, "sl_tune takes a single problem's context");
+  if ((st = check_dt(c, c->mesh, vel, t, dt)) != SL_OK) return st;
+  const sl_mesh& M = c->mesh;
+  const bool shared = uses_m2c(c, vel, opt);
+  const bool general = M.dim == 2 && c->precision == SL_MIXED && !shared;
+  auto report = [&](bool cached) {
+    if (choice) {
+      choice[0] = c->k2c_tile;
+      choice[1] = c->k2m_per_sm[0];
+      choice[2] = c->k2m_per_sm[1];
+      choice[3] = cached ? 1 : 0;
+    }
+  };
+  if (!shared && !general) {
+    report(false);
+    return SL_OK;
+  }
+  int dev = 0;
+  cudaDeviceProp prop{};
+  SL_CUDA(c, cudaGetDevice(&dev));
+  SL_CUDA(c, cudaGetDeviceProperties(&prop, dev));
+  std::string devname(prop.name);
+  for (char& ch : devname)
+    if (ch == '"' || ch == '\\') ch = '_';
+  char kbuf[512];
+  std::snprintf(kbuf, sizeof kbuf, "%s|dev=%s|n=%d|kx=%d|ky=%d|nel=%lld|mapped=%d|cons=%u|fit=%d|bv=%d|rk=%d|vel=%d",
+                shared ? "k2c_tile" : "k2m_per_sm", devname.c_str(), c->n, M.kx, M.ky, (long long)c->nel,
+                c->mapped ? 1 : 0, opt->constraints, opt->fit, opt->bvalue, opt->rk_order, vel->kind);
+  const std::string key(kbuf);
+  std::map<std::string, std::string> cache;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (cache_path) {
+    if (!read_tune_cache(cache_path, cache)) return fail(c, SL_EINVAL, "sl_tune: the cache file is not a flat JSON object");
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      int a = 0, b = 0;
+      if (shared && std::sscanf(it->second.c_str(), "tile=%d", &a) == 1 && a >= 0 && a < k2c_tile_count(c->n)) {
+        c->k2c_tile = a;
+        report(true);
+        return SL_OK;
+      }
+      if (general && std::sscanf(it->second.c_str(), "p1=%d,p2=%d", &a, &b) == 2 && a >= 0 && b >= 0) {
+        c->k2m_per_sm[0] = a;
+        c->k2m_per_sm[1] = b;
+        report(true);
+        return SL_OK;
+      }
+    }
+  }
+  // candidates: tile indices, or (phase 1, phase 2) CTAs per SM from {occupancy limit, 1, 2}
+  std::vector<std::pair<int, int>> cands;
+  if (shared) {
+    for (int k = 0; k < k2c_tile_count(c->n); ++k) cands.emplace_back(k, 0);
+  } else {
+    for (int a : {0, 1, 2})
+      for (int b : {0, 1, 2}) cands.emplace_back(a, b);
+  }
+  const int tile0 = c->k2c_tile, p10 = c->k2m_per_sm[0], p20 = c->k2m_per_sm[1];
+  auto apply = [&](const std::pair<int, int>& cd) {
+    if (shared) c->k2c_tile = cd.first;
+    else {
+      c->k2m_per_sm[0] = cd.first;
+      c->k2m_per_sm[1] = cd.second;
+    }
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(c, SL_ECUDA, std::string("sl_tune: events: ") + cudaGetErrorString(cudaGetLastError()));
+  }
+  float best = INFINITY;
+  std::pair<int, int> pick = cands[0];
+  for (const auto& cd : cands) {
+    apply(cd);
+    if ((st = sl_step(c, phi_in, phi_out, vel, t, dt, opt)) != SL_OK) break;
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = SL_ECUDA; break; }
+    for (int r = 0; r < 3 && st == SL_OK; ++r) st = sl_step(c, phi_in, phi_out, vel, t, dt, opt);
+    if (st != SL_OK) break;
+    float ms = 0.0f;
+    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = SL_ECUDA;
+      break;
+    }
+    if (ms < best) {
+      best = ms;
+      pick = cd;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SL_OK) {
+    c->k2c_tile = tile0;
+    c->k2m_per_sm[0] = p10;
+    c->k2m_per_sm[1] = p20;
+    if (st == SL_ECUDA) return fail(c, SL_ECUDA, std::string("sl_tune: ") + cudaGetErrorString(cudaGetLastError()));
+    return st;
+  }
+  apply(pick);
+  report(false);
+  if (cache_path) {
+    char vbuf[64];
+    if (shared) std::snprintf(vbuf, sizeof vbuf, "tile=%d", pick.first);
+    else std::snprintf(vbuf, sizeof vbuf, "p1=%d,p2=%d", pick.first, pick.second);
+    cache[key] = vbuf;
+    if (!write_tune_cache(cache_path, cache)) return fail(c, SL_EINVAL, "sl_tune: cannot write the cache file");
+  }
+  return SL_OK;
+}

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host API and the kernels of the GB300 DSEM-SL library.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -155,9 +156,10 @@ struct Work2M {                          // mixed workspace between the two phas
   float* faces;                          // [nel][4][6]  G_hi, G_lo (outflow flux of phi), U_out, U_in, P1, P2
   float* elem;                           // [nel][8]     r0, gx, gy, sum w psi, sum w psi^2, M^n hi, lo, unused
 };
+// per_sm: resident CTAs per SM of the persistent grid (0: as many as the occupancy allows)
 void launch_step2d_mixed(int phase, int n, const StepParams& p, const Mixed2DExtra& x, const Map2D& m,
                          int64_t count, const float* in, float* out, const Work2M& w, unsigned* status,
-                         cudaStream_t s);
+                         cudaStream_t s, int per_sm);
 inline int64_t work2m_floats(int64_t nel, int n) { return nel * (int64_t)(n * n + 4 * n + 24 + 8); }
 constexpr int WORK2M_FACE = 24, WORK2M_ELEM = 8;   // floats per element of the face and element records
 
@@ -188,8 +190,11 @@ struct Mixed2DConstParams {
 };
 bool build_mixed2d_const(const sl_ctx* c, double a, double b, double dt, unsigned cons, int rk,
                          std::vector<float>& buf, Mixed2DConstParams& P, std::string& err);
+// tile: index of the compiled tile shape (0: default; k2c_tile_count candidates per node count)
 void launch_step2d_const(const Mixed2DConstParams& p, const float* tab, const float* in, float* out, unsigned* status,
-                         cudaStream_t s);
+                         cudaStream_t s, int tile);
+int k2c_tile_count(int n);
+void k2c_tile_shape(int n, int tile, int* tx, int* ty);
 
 // Kernel parameter block of the 1D shared-operator (mixed precision) step; passed by value.
 struct Mixed1DParams {
@@ -222,6 +227,8 @@ void launch_pack(int64_t nvals, int64_t plane, const double* src, float* dst, cu
 // after raising the kernel's dynamic shared-memory limit to smem) times the SM count; cached per
 // (device, kernel, threads, smem) under a lock, so host threads on several devices may launch at once.
 int persistent_grid(const void* kernel, int threads, size_t smem);
+// SMs of the current device (cached per device)
+int sm_count();
 // Raise a kernel's dynamic shared-memory allowance on the current device to bytes (once per device,
 // kernel and size; needed when its static plus dynamic shared memory exceeds 48 KB).
 void allow_dynamic_smem(const void* kernel, size_t bytes);
@@ -331,5 +338,9 @@ struct sl_ctx {
   const double* inflow = nullptr;
   int64_t inflow_stride = 0;
   const double* inflow_step = nullptr;
+  // launch shapes chosen by the autotuner (sl_tune): the shared-operator kernel's tile, and the
+  // resident CTAs per SM of the general mixed kernels' two phases (0: the defaults)
+  int k2c_tile = 0;
+  int k2m_per_sm[2] = {0, 0};
   std::string err;
 };
