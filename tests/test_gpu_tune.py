@@ -1,7 +1,9 @@
 """The launch-shape autotuner (sl_tune): it picks among compiled tile shapes (elements per CTA) of
 the 2D shared-operator kernel and among resident-CTA counts of the general mixed kernels'
 persistent grids, records the choice in a JSON cache, and applies a cached choice without timing.
-Every shape computes each element with the same arithmetic: results are bitwise equal."""
+The grid size leaves every element's arithmetic as it is (bitwise equal results); the tile shapes
+are separate compilations of the same per-element arithmetic, whose floating-point contractions
+the compiler may schedule differently, so they agree to the float rounding of the increments."""
 import json
 
 import numpy as np
@@ -54,7 +56,7 @@ def test_tune_shared_operator_tiles(sl, tmp_path, n):
     # the same key again: applied from the cache, no timing
     ctx2, a2, _, _ = _setup(sl, 13, 11, n, vel, sl.C_BOUNDARY | sl.C_MASS, bc=1, ghost=0.2)
     assert ctx2.tune(a2, ctx2.new_state(), vel, 0.1, dt, opts, cache)["cached"]
-    # every candidate tile gives the same bits
+    # every candidate tile gives the same result to float rounding
     outs = []
     for tile in range(3 if n <= 12 else 2):
         _force(cache, "k2c_tile|", f"tile={tile}")
@@ -64,9 +66,10 @@ def test_tune_shared_operator_tiles(sl, tmp_path, n):
         out = c.new_state()
         c.step(a, out, vel, 0.1, dt, opts)
         assert c.sync() == 0
-        outs.append(out)
+        outs.append(c.unpack(out))
     for o in outs[1:]:
-        assert torch.equal(o, outs[0])
+        rel = ((o - outs[0]).norm() / outs[0].norm()).item()
+        assert rel <= 1e-7, rel                  # a wrong shape would differ at O(1)
 
 
 def test_tune_general_kernel_per_sm(sl, tmp_path):
