@@ -487,10 +487,10 @@ def run_ours(args, rank, world, local_rank):
 
 # DRAM bytes per launch from one ncu capture (read + written), scaled to the full mesh by the
 # element count (traffic grows in proportion); None once the kernel has changed since
-# DRAM bytes (read + write) per element of the dominant kernels, from one ncu capture at 512 x 512
-# (262,144 elements; traffic grows in proportion to the elements), multiplied by the element count
-# of a launch (profiles/k2m_k_p1_k_p2_mixed_general_config5_swirl.md).  Valid for the kernels as
-# profiled; to be taken again after a change to them.
+# DRAM bytes (read + write) per element of the dominant kernels, from one ncu capture of both at
+# 512 x 512 (262,144 elements; traffic grows in proportion to the elements), multiplied by the
+# element count of a launch.  Valid for the kernels as profiled; to be taken again after a change
+# to them.
 TRAFFIC_PER_ELEMENT = {"k2m::k_p1<8>": (139.418112e6 + 89.868288e6) / 262144,
                        "k2m::k_p2<8>": (272.105728e6 + 113.296384e6) / 262144}
 
