@@ -351,7 +351,7 @@ def run_ours(args, rank, world, local_rank):
     phi0_dev = device_initial_state(torch, ctx, prob)
     a = ctx.pack(phi0_dev)
     b = ctx.new_state()
-    tuned = ctx.tune(a, b, vel, 0.0, dt, opts, tune_cache_path())   # launch shapes (sl_tune)
+    tuned = autotune(sl, ctx, a, b, vel, 0.0, dt, opts)             # launch shapes (sl_tune)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     # one step from t = 0 for the accuracy check against the oracle
     ctx.step(a, b, vel, 0.0, dt, opts)
@@ -514,7 +514,7 @@ def measure_config(sl, torch, prob, precision, steps, flush, phi=None):
     opts = sl.options(prob.constraints, prob.rk_order)
     a, b = ctx.pack(phi0), ctx.new_state()
     stream = ctx.stream
-    tuned = ctx.tune(a, b, vel, 0.0, dt, opts, tune_cache_path())   # launch shapes (sl_tune)
+    tuned = autotune(sl, ctx, a, b, vel, 0.0, dt, opts)             # launch shapes (sl_tune)
     ctx.step(a, b, vel, 0.0, dt, opts)           # warm-up
     torch.cuda.synchronize()
     ms, a, b, _ = _time_steps(torch, ctx, stream, b, a, vel, dt, opts, dt, steps, flush)
@@ -527,14 +527,29 @@ def measure_config(sl, torch, prob, precision, steps, flush, phi=None):
 
 
 def tune_cache_path():
-    """The autotuner's JSON cache: SL_TUNE_CACHE, else the user's cache directory."""
+    """The autotuner's JSON cache: SL_TUNE_CACHE, else the user's cache directory (None when that
+    cannot be created: the tuner then times without a cache)."""
     p = os.environ.get("SL_TUNE_CACHE")
     if not p:
         d = os.path.join(os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache")),
                          "paper_1910_06476_gb300")
-        os.makedirs(d, exist_ok=True)
+        try:
+            os.makedirs(d, exist_ok=True)
+        except OSError:
+            return None
         p = os.path.join(d, "tune.json")
     return p
+
+
+def autotune(sl, ctx, a, b, vel, t, dt, opts):
+    """sl_tune with the cache; a cache that cannot be read or written falls back to timing without
+    one (the choice is then reported with the reason)."""
+    try:
+        return ctx.tune(a, b, vel, t, dt, opts, tune_cache_path())
+    except sl.SlError as e:
+        r = ctx.tune(a, b, vel, t, dt, opts, None)
+        r["cache_error"] = str(e)
+        return r
 
 
 def secondary_configs(sl, torch, flush, full=False, only=None):
