@@ -6,6 +6,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -56,8 +57,14 @@ def build(force=False, verbose=False, extra=None):
     if not force and not _stale():
         return OUT
     os.makedirs(OBJDIR, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=max(2, min(16, os.cpu_count() or 2))) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra), sources()))
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        cores = os.cpu_count() or 2
+    # the kernel instantiation units (k_*_{a..d}.cu) take longest: start them first
+    srcs = sorted(sources(), key=lambda f: (not re.search(r"_[a-d]\.cu$", f), f))
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(16, cores))) as ex:
+        results = list(ex.map(lambda s: _compile(s, extra), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for _, err in results:
