@@ -881,7 +881,8 @@ sl_status sl_run(sl_ctx* c, void* phi_a, void* phi_b, const sl_velocity* vel, do
         cudaEventCreateWithFlags(&c->run_ev[1], cudaEventDisableTiming) != cudaSuccess)
       return fail(c, SL_ECUDA, std::string("run stream: ") + cudaGetErrorString(cudaGetLastError()));
   }
-  std::vector<double> key = {(double)vel->kind, t0, dt, (double)nsteps, (double)opt->constraints,
+  std::vector<double> key = {(double)c->k2c_tile, (double)c->k2m_per_sm[0], (double)c->k2m_per_sm[1],
+                             (double)vel->kind, t0, dt, (double)nsteps, (double)opt->constraints,
                              (double)opt->rk_order, (double)opt->fit, (double)opt->bvalue, opt->picard_rtol,
                              (double)opt->picard_cap, (double)(uintptr_t)phi_a, (double)(uintptr_t)phi_b,
                              (double)(uintptr_t)c->inflow, (double)c->inflow_stride,
